@@ -1,0 +1,312 @@
+"""Benchmark: MW forward + inverse transforms/s at L = 2048, 16 maps (8 spin 0,
+8 spin 2), complex Gaussian f_lm with E|f_lm|^2 = 1/(l+1)^2.
+
+One step = inverse transform of the batch followed by the forward transform of
+the result (the round trip of the paper's protocol, Sec. V-D): 2B transforms.
+Inputs (1.1 GB of f_lm, 2.1 GB of maps) are larger than L2, so no flush is
+needed between steps.  value: device-timed (CUDA events on the stream) with
+inputs resident in HBM.  e2e: the same round trip through the C ABI with pinned
+host buffers, host<->device copies inside the timed region.  The roofline entry
+describes the dominant stage, timed live with the library's per-stage events.
+
+--impl reference runs the FP64 CPU oracle (the only baseline this project has)
+on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank transforms its own batch (weak scaling, no
+data-path collective); value = all ranks' transforms / max rank time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MW fwd+inv transforms/s at L=2048,B=16 (mixed vs FP64 GPU) at ≤1e-6 rel err"
+L_BENCH, B_BENCH = 2048, 16
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def peaks():
+    pk = {"hbm_gbs": 6794.8, "bf16_tflops": 1899.0, "bf16_tflops_sustained": 1700.8, "src": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            j = json.load(fh)
+        pk.update({k: j[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in j})
+        pk["src"] = "measured"
+    except Exception:
+        pass
+    # FP64 CUDA-core FMA peak: own DFMA microbenchmark on this machine's GB300
+    # (profiles/gb300_fp64_peaks.md); no FP64 entry exists in MEASURED_PEAKS.json.
+    pk["fp64_tflops"] = 0.993
+    return pk
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.idx, self.proc, self.lines = gpu_index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + CLOCK_Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def contraction_units(L, spins):
+    """(l, m, m' >= 0, map) multiply-accumulates of one direction's Delta contraction."""
+    tot = 0
+    for s in spins:
+        for l in range(abs(s), L):
+            tot += (2 * l + 1) * (l + 1)
+    return tot
+
+
+def risbo_units(L):
+    """Quarter-plane element updates of one Risbo sweep (two half steps per l)."""
+    tot = 0
+    for l in range(1, L):
+        tot += l * l + (l + 1) * (l + 1)
+    return tot
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1110_6298_gb300 import build as lib_build
+    from paper_1110_6298_gb300 import mw, workloads as wl
+
+    if rank == 0 or world == 1:
+        lib_build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = wl.workload_l2048_b16(L=args.L)
+    L, spins = w["L"], w["spins"]
+    B = len(spins)
+    flm_h = torch.from_numpy(np.stack(w["flm"]))
+    flm = flm_h.to(dev)
+    plan = mw.Plan(L, spins, precision=args.precision)
+    maps = torch.empty((B, mw.map_size(L)), dtype=torch.complex128, device=dev)
+    out = torch.empty_like(flm)
+    stream = torch.cuda.current_stream(dev)
+
+    launches_per_step = 0
+    for _ in range(args.warmup):
+        plan.inverse(flm, out=maps)
+        n1 = plan.last_launches
+        plan.forward(maps, out=out)
+        launches_per_step = n1 + plan.last_launches
+    torch.cuda.synchronize(dev)
+    err = float((out - flm).abs().max().item() / flm.abs().max().item())
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    plan.set_timing(True)
+    plan.stage_times(reset=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.inverse(flm, out=maps)
+        plan.forward(maps, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stages = plan.stage_times(reset=True)
+    plan.set_timing(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2 * B * args.steps / (ms / 1e3)
+
+    # end to end: pinned host buffers through the C ABI, copies inside the timed region
+    flm_pin = flm_h.pin_memory()
+    map_pin = torch.empty((B, mw.map_size(L)), dtype=torch.complex128).pin_memory()
+    out_pin = torch.empty_like(flm_pin).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    plan.inverse(flm_pin, out=map_pin)
+    plan.forward(map_pin, out=out_pin)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.inverse(flm_pin, out=map_pin)
+        plan.forward(map_pin, out=out_pin)
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * 2 * B * e2e_steps / t_e2e
+    bytes_flm = B * L * L * 16
+    bytes_map = B * mw.map_size(L) * 16
+
+    # roofline of the dominant stage
+    pk = peaks()
+    dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k][0])
+    t_dom_s = stages[dom][0] / 1e3
+    if dom == "contract":
+        flops = 2 * args.steps * contraction_units(L, spins) * 4  # complex x real MAC = 4 flops
+        achieved = flops / t_dom_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["fp64_tflops"], "traffic": None, "kernel": "k_contract_forward/inverse",
+                "peak_src": "measured (own FP64 DFMA microbenchmark)"}
+    elif dom == "delta":
+        flops = 2 * args.steps * risbo_units(L) * 7  # 4-point stencil: 4 mul + 3 add
+        achieved = flops / t_dom_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["fp64_tflops"], "traffic": None, "kernel": "k_risbo_half",
+                "peak_src": "measured (own FP64 DFMA microbenchmark)"}
+    else:
+        byts = args.steps * (bytes_flm + bytes_map) * 2
+        achieved = byts / t_dom_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_src": pk["src"]}
+    result = {
+        "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32+bf16",
+        "data": "synthetic (seeded complex Gaussian f_lm, C_l=1/(l+1)^2)",
+        "config": {"workload": f"MW round trip L={L}, B={B} (8 maps s=0, 8 maps s=2)", "L": L, "batch": B,
+                   "spins": spins, "precision": args.precision, "l2_flush": "inputs larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roundtrip_rel_err": err,
+        "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
+                "d2h_bytes_per_step": bytes_map + bytes_flm},
+        "gpu_launches": launches_per_step * args.steps,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "roofline": roof,
+        "clocks": ck,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, quick=False)
+    return result
+
+
+def cpu_baseline(w, quick=False):
+    """FP64 oracle round trip of one map of the workload on the host cores."""
+    import numpy as np
+
+    import oracle
+    L, s = w["L"], w["spins"][0]
+    f = np.asarray(w["flm"][0])
+    t0 = time.perf_counter()
+    m = oracle.inverse(f, L, s)
+    oracle.forward(m, L, s)
+    t = time.perf_counter() - t0
+    return {"value": 2.0 / t, "unit": "transforms/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one map (spin {s}) of the L={L} workload: oracle inverse + forward, {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_1110_6298_gb300 import workloads as wl
+    w = wl.workload_l2048_b16(n_maps=2, L=args.L)
+    for _ in range(args.warmup):
+        cpu_baseline(w)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cb = cpu_baseline(w)
+    t = time.perf_counter() - t0
+    value = 2.0 * args.steps / t
+    cb["value"] = value
+    cb["sample"] = f"each step: one map of the L={args.L} workload, oracle inverse + forward"
+    return {"metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"MW round trip L={args.L}, one map per step (oracle sample)"},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--L", type=int, default=L_BENCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

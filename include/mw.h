@@ -1,0 +1,139 @@
+/*
+ * mw.h -- C ABI of libmw: GB300 (sm_103a) MW spin spherical harmonic transforms.
+ *
+ * The transforms are those of McEwen & Wiaux, "A novel sampling theorem on the
+ * sphere", IEEE Trans. Signal Process. 59(12), 2011:
+ *   inverse  f_lm -> f(theta_t, phi_p)   Sec. IV-E, Eqs. (Fmm), (Fmt), (f_pfft)
+ *   forward  f(theta_t, phi_p) -> f_lm   Sec. IV-D, Eqs. (Gmt), (Gmm_convolution),
+ *                                        (flm_wig)
+ * for band limit L (f_lm = 0 for l >= L) and integer spin s with |s| < L, on the
+ * equiangular grid of Sec. IV-C:
+ *   theta_t = pi (2t+1) / (2L-1),  t = 0..L-1   (theta_{L-1} = pi, the south pole)
+ *   phi_p   = 2 pi p / (2L-1),     p = 0..2L-2
+ * which holds N_MW = (L-1)(2L-1) + 1 samples.
+ *
+ * Buffer layouts (all complex numbers are interleaved double pairs (re, im),
+ * i.e. C99 double complex / numpy complex128):
+ *   map : N_MW values per map: rings t = 0..L-2, each 2L-1 samples in phi_p
+ *         order, then ONE pole sample f(pi, phi = 0).  A spin-s signal on the
+ *         pole ring equals f(pi, 0) e^{i s phi}, because d^l_{m,-s}(pi) vanishes
+ *         unless m = s (Eq. wignerd_sym2 at beta = 0), so the one sample fixes it.
+ *   flm : L*L values per map, f_lm at index l*l + l + m.  Spin-s harmonics exist
+ *         only for l >= |s| (Sec. III-B): such entries are written as 0 by the
+ *         forward transform and ignored on input by the inverse.
+ *   A batch of B maps is B such blocks back to back.
+ *
+ * Pointers may be device memory or host memory (pageable or pinned); host
+ * buffers are staged through plan-owned device buffers with cudaMemcpyAsync on
+ * the call's stream.  Inputs are never modified.  Outputs must not alias inputs.
+ * All data pointers stay owned by the caller; the plan owns its workspace and
+ * tables and frees them in mw_plan_destroy.
+ *
+ * Calls are enqueued on `stream` (a cudaStream_t; NULL means the legacy default
+ * stream) and return before the GPU finishes; device memory results are valid
+ * once the stream reaches them, host outputs once the call returns (the call
+ * synchronises the stream when it has to copy results to host memory).  A plan
+ * must not be used by two host threads at once, nor by two streams whose work
+ * overlaps.  For a given plan and input the results are bitwise reproducible:
+ * every reduction runs in a fixed order and no atomics touch the data.
+ *
+ * Errors: every function returns a status; MW_EINVAL for bad arguments (checked
+ * before anything is enqueued), MW_ENOMEM when a device or host allocation
+ * fails, MW_ECUDA when a CUDA call or launch fails (the plan stays usable if
+ * the context does), MW_EUNSUPPORTED for valid but unimplemented requests.
+ */
+#ifndef MW_H
+#define MW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mw_plan mw_plan; /* opaque; created by mw_plan_create*, freed by mw_plan_destroy */
+
+typedef enum {
+  MW_OK = 0,
+  MW_EINVAL = 1,
+  MW_ENOMEM = 2,
+  MW_ECUDA = 3,
+  MW_ETIMEOUT = 4,
+  MW_EUNSUPPORTED = 5
+} mw_status;
+
+/* Precision of a plan (flags & 0xff).
+ * MW_PREC_FP64 : every stage in IEEE double.
+ * MW_PREC_MIXED: the Wigner-Delta recursion (Risbo, Sec. V-B) in double; the
+ *                Delta contraction on the tensor cores (tcgen05) as split-BF16
+ *                products with FP32 accumulation and a double sum across
+ *                m'-chunks; the FFT stages in single precision.  Designed for a
+ *                relative error below 1e-6 against the FP64 path. */
+enum { MW_PREC_FP64 = 0, MW_PREC_MIXED = 1 };
+
+/* Create a plan for `batch` maps of band limit L and spin s.
+ * Requires 1 <= L <= 2048, |s| < L, batch >= 1, out != NULL.  Allocates the
+ * device workspace on the current CUDA device; *out is NULL on failure. */
+mw_status mw_plan_create(mw_plan **out, int L, int s, int batch, unsigned flags);
+
+/* As mw_plan_create, with one spin per map: spins[b] is the spin of map b
+ * (|spins[b]| < L).  Maps of different spin share each Wigner-Delta plane,
+ * which depends on neither L nor s (Sec. V footnote on multiple spins). */
+mw_status mw_plan_create_spins(mw_plan **out, int L, int batch, const int *spins, unsigned flags);
+
+/* Forward transform (Sec. IV-D): map_in [batch][N_MW] -> flm_out [batch][L*L].
+ * The result is that of the paper's algorithm: phi DFT of each ring (Eq. Gmt
+ * discretised), periodic extension in theta with parity (-1)^(m+s), theta DFT
+ * to F_mm', quadrature-weight convolution Eq. (Gmm_convolution), and the Wigner
+ * sum Eq. (flm_wig).  It is exact for band-limited maps (forward(inverse(f)) = f)
+ * and defined by those steps for any other map. */
+mw_status mw_forward(mw_plan *plan, const void *map_in, void *flm_out, void *stream);
+
+/* Inverse transform (Sec. IV-E): flm_in [batch][L*L] -> map_out [batch][N_MW]
+ * through Eq. (Fmm) (with F_{m,-m'} = (-1)^(m+s) F_mm', Eq. Fmm_sym1),
+ * Eq. (Fmt) and Eq. (f_pfft); it equals the synthesis sum_lm f_lm sY_lm on the
+ * grid. */
+mw_status mw_inverse(mw_plan *plan, const void *flm_in, void *map_out, void *stream);
+
+/* Hermitian adjoints (not in the paper; used for gradients):
+ * mw_forward_adjoint: flm_in [batch][L*L] -> map_out [batch][N_MW], = forward^H.
+ * mw_inverse_adjoint: map_in [batch][N_MW] -> flm_out [batch][L*L], = inverse^H.
+ * Each runs the stages of its transform in reverse order, conjugated; the
+ * Wigner-Delta planes are recomputed, never stored. */
+mw_status mw_forward_adjoint(mw_plan *plan, const void *flm_in, void *map_out, void *stream);
+mw_status mw_inverse_adjoint(mw_plan *plan, const void *map_in, void *flm_out, void *stream);
+
+/* Free a plan and its workspace.  NULL-safe.  Synchronises the device. */
+mw_status mw_plan_destroy(mw_plan *plan);
+
+/* Static description of a status code. */
+const char *mw_status_string(mw_status st);
+
+/* Buffer sizes in complex elements per map: (L-1)(2L-1)+1 and L*L (0 for L < 1). */
+size_t mw_map_size(int L);
+size_t mw_flm_size(int L);
+
+/* Plan introspection: bytes of device workspace held, and the number of
+ * kernels the last call on this plan launched. */
+size_t mw_plan_workspace_bytes(const mw_plan *plan);
+int mw_plan_last_launches(const mw_plan *plan);
+
+/* Per-stage timing (diagnostics, not in the paper).  With timing enabled, each
+ * call records CUDA events on its stream around every stage:
+ *   MW_STAGE_PHI     phi DFTs (and their adjoints)
+ *   MW_STAGE_THETA   theta extension / DFT / weight convolution (and adjoints)
+ *   MW_STAGE_DELTA   Risbo recursion of the Wigner-Delta planes
+ *   MW_STAGE_CONTRACT Delta contraction (forward or inverse sum)
+ * mw_plan_stage_times waits for the recorded events, adds their durations to
+ * running totals and returns them: ms[MW_NUM_STAGES] milliseconds and
+ * launches[MW_NUM_STAGES] kernel launches since the last reset (either pointer
+ * may be NULL); reset != 0 clears the totals afterwards. */
+enum { MW_STAGE_PHI = 0, MW_STAGE_THETA = 1, MW_STAGE_DELTA = 2, MW_STAGE_CONTRACT = 3, MW_NUM_STAGES = 4 };
+mw_status mw_plan_set_timing(mw_plan *plan, int enable);
+mw_status mw_plan_stage_times(mw_plan *plan, double *ms, long long *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MW_H */

@@ -247,22 +247,26 @@ int orc_inverse_rings(int L, int s, int nmaps, const double *flm, int nth, const
     const double *D = sw.cur;
     const double Nl = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
     /* sum over m' in ascending order for every (theta_r, m); the loop over m is
-     * innermost so that plane rows are read contiguously */
-#pragma omp parallel for schedule(static)
-    for (int r = 0; r < nth; ++r) {
+     * innermost so that plane rows are read contiguously; threads take (ring,
+     * block of m) pairs */
+    const int nblk = (P + 63) / 64;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int task = 0; task < nth * nblk; ++task) {
+      const int r = task / nblk, m_lo = -l + (task % nblk) * 64;
+      const int m_hi = (m_lo + 63 < l) ? m_lo + 63 : l;
       double *acc = dth + 2 * (size_t)r * M;
-      for (int m = -l; m <= l; ++m) { acc[2 * (m + L - 1)] = 0.0; acc[2 * (m + L - 1) + 1] = 0.0; }
+      for (int m = m_lo; m <= m_hi; ++m) { acc[2 * (m + L - 1)] = 0.0; acc[2 * (m + L - 1) + 1] = 0.0; }
       for (int mp = -l; mp <= l; ++mp) {
         const double w = D[(size_t)(mp + l) * P + (-s + l)];
         const double er = ex[2 * ((size_t)r * M + mp + L - 1)], ei = ex[2 * ((size_t)r * M + mp + L - 1) + 1];
         const double *row = D + (size_t)(mp + l) * P;
-        for (int m = -l; m <= l; ++m) {
+        for (int m = m_lo; m <= m_hi; ++m) {
           const double k = row[m + l] * w;
           acc[2 * (m + L - 1)] += k * er;
           acc[2 * (m + L - 1) + 1] += k * ei;
         }
       }
-      for (int m = -l; m <= l; ++m) {  /* times i^(-s-m) */
+      for (int m = m_lo; m <= m_hi; ++m) {  /* times i^(-s-m) */
         double pr, pi_;
         ipow(-s - m, &pr, &pi_);
         const double ar = acc[2 * (m + L - 1)], ai = acc[2 * (m + L - 1) + 1];

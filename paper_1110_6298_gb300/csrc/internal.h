@@ -1,0 +1,93 @@
+// internal.h -- plan layout and kernel entry points shared by the libmw sources.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/mw.h"
+
+// Radix sequence of one FFT length (passed by value to kernels).
+struct FftDesc {
+  int n;
+  int nrad;
+  int rad[26];
+};
+
+// Maps that share a spin are contracted together against one Delta plane.
+// Each group holds at most kMaxGroupMaps maps (larger spin classes are split).
+constexpr int kMaxGroupMaps = 32;
+constexpr int kChunk = 64;  // Delta planes staged per contraction launch
+
+struct SpinGroup {
+  int s;
+  int nb;
+  int maps[kMaxGroupMaps];
+};
+
+struct mw_plan {
+  int L = 0, B = 0, M = 0, N = 0;
+  unsigned flags = 0;
+  int prec = MW_PREC_FP64;
+  int device = 0;
+  std::vector<int> spins;          // per map
+  std::vector<SpinGroup> groups;   // host copy
+  SpinGroup* d_groups = nullptr;   // device copy
+  int* d_spins = nullptr;
+
+  FftDesc fM{}, fN{};
+  int fft_threads = 0;             // block size of the FFT kernels
+  // tables, precision of the FFT stages (double2 or float2 per entry)
+  void* d_twM = nullptr;           // e^{-2 pi i k / M}, k < M
+  void* d_twN = nullptr;           // e^{-2 pi i k / N}, k < N
+  void* d_phase = nullptr;         // e^{-i pi m' / M}, m' = -(L-1)..L-1 (index m'+L-1)
+  void* d_V = nullptr;             // DFT_N of the reflected weights, pre-scaled by 1/(N M)
+  double* d_sqrt = nullptr;        // sqrt(k), k = 0..2L+2
+  double2* d_upole = nullptr;      // u(m') + u(-m') (m' > 0), u(0): pole row of the forward adjoint
+
+  // workspace
+  void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
+  double2* d_Gp = nullptr;         // [B][M][L] folded G+_{m,m'} or F+_{m,m'}, m' >= 0
+  double* d_S = nullptr;           // [kChunk][LD][LD] staged integer Delta planes (quarter)
+  double* d_H = nullptr;           // [LD][LD] half-integer plane
+  int LD = 0;                      // plane row stride (L+1)
+  double2* d_map_stage = nullptr;  // host-pointer staging
+  double2* d_flm_stage = nullptr;
+
+  size_t ws_bytes = 0;
+  int last_launches = 0;
+
+  // optional per-stage timing (CUDA events on the call's stream)
+  bool timing = false;
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> recs;           // pending event pairs of recorded calls
+  std::vector<cudaEvent_t> pool;   // free events
+  double stage_ms[MW_NUM_STAGES] = {0};
+  long long stage_launches[MW_NUM_STAGES] = {0};
+};
+
+// Event pair around a span of launches of one stage (no-op unless timing is on).
+struct StageSpan {
+  mw_plan* p;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageSpan(mw_plan* p_, int stage_, cudaStream_t st_);
+  void end(int launches);
+};
+
+// ---- kernels (launch helpers return cudaGetLastError()) ----
+cudaError_t launch_phi_forward(const mw_plan* p, const double2* map, cudaStream_t st);
+cudaError_t launch_theta_forward(const mw_plan* p, cudaStream_t st);
+cudaError_t launch_theta_inverse(const mw_plan* p, cudaStream_t st);
+cudaError_t launch_phi_inverse(const mw_plan* p, double2* map, cudaStream_t st);
+cudaError_t launch_phi_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st);
+cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st);
+cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st);
+cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st);
+cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st);
+
+// Wigner stage: sweep l = 0..L-1 with Risbo's recursion and contract.
+// mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
+cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out,
+                       cudaStream_t st, int* launches);

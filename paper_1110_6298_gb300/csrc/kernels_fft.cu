@@ -1,0 +1,515 @@
+// kernels_fft.cu -- the O(L^2 log L) stages of the MW transforms and their adjoints.
+//
+// Forward (Sec. IV-D):
+//   phi_forward   : G_m(theta_t) = 2pi/M sum_p f(theta_t, phi_p) e^{-i m phi_p}, one
+//                   block per ring; the pole ring f(pi,0) e^{i s phi} transforms in
+//                   closed form to 2 pi f(pi,0) delta_{m,s}.
+//   theta_forward : one block per (m, map): periodic extension with parity
+//                   (-1)^(m+s), DFT over the 2L-1 extended nodes with the half-sample
+//                   phase e^{-i m' pi/M} (F_mm'), zero-pad to N >= 4L-3, inverse DFT,
+//                   product with the DFT of the reflected weights, DFT back
+//                   (Eq. Gmm_convolution), then the +-m' fold
+//                   G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'} used by the Wigner stage.
+// Inverse (Sec. IV-E):
+//   theta_inverse : one block per (m, map): phase (-1)^s i^-(m+s) of Eq. (Fmm),
+//                   unfold F_{m,-m'} = (-1)^(m+s) F_mm' (Eq. Fmm_sym1), inverse DFT over
+//                   the extended nodes (Eq. Fmt), keep t < L.
+//   phi_inverse   : one block per ring: inverse DFT in phi (Eq. f_pfft); the pole
+//                   ring keeps its phi = 0 sample.
+// Adjoints: each stage transposed and conjugated, run in reverse order.
+//
+// T is the arithmetic type of these stages (double for the FP64 path, float for
+// the mixed path).  Map and f_lm buffers are always complex double.
+#include <cmath>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace {
+
+template <typename T>
+using C = typename cplx<T>::t;
+
+template <typename T>
+__device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {  // a * conj(b)
+  return mkc<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T>
+__device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
+template <typename T>
+__device__ __forceinline__ C<T> from64(double2 v) { return mkc<T>((T)v.x, (T)v.y); }
+__device__ __forceinline__ double2 to64(double2 v) { return v; }
+__device__ __forceinline__ double2 to64(float2 v) { return make_double2(v.x, v.y); }
+
+// (-1)^k for any integer k
+__device__ __forceinline__ int parity_sign(int k) { return (k & 1) ? -1 : 1; }
+
+// i^k as (re, im)
+__device__ __forceinline__ double2 ipow(int k) {
+  const int r = k & 3;  // two's complement keeps k mod 4 for negative k
+  return make_double2(r == 0 ? 1.0 : (r == 2 ? -1.0 : 0.0), r == 1 ? 1.0 : (r == 3 ? -1.0 : 0.0));
+}
+
+struct Dims {
+  int L, M, N, B;
+  long long nmw;  // samples per map
+};
+
+__device__ __forceinline__ int spin_of(const int* spins, int b) { return spins[b]; }
+
+// --------------------------------------------------------------------------
+// forward
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const double2* __restrict__ map,
+                              C<T>* __restrict__ Gt /* [B][M][L] */, const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int t = blockIdx.x, b = blockIdx.y;
+  const int L = d.L, M = d.M;
+  const double2* f = map + (long long)b * d.nmw;
+  C<T>* out = Gt + (long long)b * M * L;
+  if (t == L - 1) {  // pole ring: 2 pi f(pi,0) delta_{m,s}
+    const int s = spin_of(spins, b);
+    const double2 fp = f[(long long)(L - 1) * M];
+    const T tp = (T)(2.0 * M_PI);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const int m = i - (L - 1);
+      out[(long long)i * L + t] = (m == s) ? mkc<T>((T)fp.x * tp, (T)fp.y * tp) : mkc<T>(0, 0);
+    }
+    return;
+  }
+  for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = from64<T>(f[(long long)t * M + p]);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  const T sc = (T)(2.0 * M_PI / M);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const int m = i - (L - 1);
+    const int k = m < 0 ? m + M : m;
+    out[(long long)i * L + t] = cscale<T>(buf[k], sc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
+                                const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
+                                const C<T>* __restrict__ V, const C<T>* __restrict__ Gt, double2* __restrict__ Gp,
+                                const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M, N = d.N;
+  const int im = blockIdx.x, b = blockIdx.y;
+  const int m = im - (L - 1);
+  const int s = spin_of(spins, b);
+  const T sg = (T)parity_sign(m + s);
+  const C<T>* g = Gt + ((long long)b * M + im) * L;
+  // periodic extension over the 2L-1 nodes
+  for (int t = threadIdx.x; t < M; t += blockDim.x)
+    buf[t] = (t < L) ? g[t] : cscale<T>(g[2 * L - 2 - t], sg);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  // F_mm' (times M 2pi, folded into V) with the half-sample phase, zero-padded to N
+  C<T> v[kFftVPT];
+#pragma unroll
+  for (int r = 0; r < kFftVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < N) {
+      int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
+      if (mp == 0x7fffffff) v[r] = mkc<T>(0, 0);
+      else v[r] = cmul<T>(buf[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kFftVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < N) buf[k] = v[r];
+  }
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fN, twN, true);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmul<T>(buf[k], V[k]);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fN, twN, false);
+  // fold m' >= 0: G+_{m,0} = G_m0, G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'}
+  double2* out = Gp + ((long long)b * M + im) * L;
+  for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
+    double2 a = to64(buf[mp]);
+    if (mp > 0) {
+      const double2 c = to64(buf[N - mp]);
+      a.x += (double)sg * c.x;
+      a.y += (double)sg * c.y;
+    }
+    out[mp] = a;
+  }
+}
+
+// --------------------------------------------------------------------------
+// inverse
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ phase,
+                                const double2* __restrict__ Gp, C<T>* __restrict__ Gt /* [B][L][M] */,
+                                const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M;
+  const int im = blockIdx.x, b = blockIdx.y;
+  const int m = im - (L - 1);
+  const int s = spin_of(spins, b);
+  const double sg = (double)parity_sign(m + s);
+  // (-1)^s i^-(m+s)
+  double2 ph = ipow(-(m + s));
+  if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+  const double2* in = Gp + ((long long)b * M + im) * L;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const int mp = (k <= L - 1) ? k : k - M;  // slot of m' in the length-M DFT
+    const int a = mp < 0 ? -mp : mp;
+    double2 x = in[a];
+    if (mp < 0) { x.x *= sg; x.y *= sg; }
+    const double2 y = make_double2(ph.x * x.x - ph.y * x.y, ph.x * x.y + ph.y * x.x);
+    // times e^{+i m' pi / M} = conj(phase)
+    buf[k] = cmulc<T>(mkc<T>((T)y.x, (T)y.y), phase[mp + L - 1]);
+  }
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  C<T>* out = Gt + (long long)b * L * M;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) out[(long long)t * M + im] = buf[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ Gt,
+                              double2* __restrict__ map) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M;
+  const int t = blockIdx.x, b = blockIdx.y;
+  const C<T>* in = Gt + ((long long)b * L + t) * M;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const int m = (k <= L - 1) ? k : k - M;
+    buf[k] = in[m + L - 1];
+  }
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  double2* f = map + (long long)b * d.nmw;
+  if (t < L - 1) {
+    for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(buf[p]);
+  } else if (threadIdx.x == 0) {
+    f[(long long)(L - 1) * M] = to64(buf[0]);
+  }
+}
+
+// --------------------------------------------------------------------------
+// adjoint of the forward: Wigner^H (run_wigner mode 1) -> theta_forward^H -> phi_forward^H
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
+                                        const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
+                                        const C<T>* __restrict__ V, const double2* __restrict__ Gp,
+                                        C<T>* __restrict__ Gt /* [B][L][M] */, const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M, N = d.N;
+  const int im = blockIdx.x, b = blockIdx.y;
+  const int m = im - (L - 1);
+  const int s = spin_of(spins, b);
+  const double sg = (double)parity_sign(m + s);
+  double2 ph = ipow(-(m + s));  // conj of (-1)^s i^(m+s)
+  if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+  const double2* in = Gp + ((long long)b * M + im) * L;
+  // G^H_mm' for |m'| <= L-1, zero-padded to N
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
+    if (mp == 0x7fffffff) { buf[k] = mkc<T>(0, 0); continue; }
+    const int a = mp < 0 ? -mp : mp;
+    double2 x = in[a];
+    if (mp < 0) { x.x *= sg; x.y *= sg; }
+    buf[k] = mkc<T>((T)(ph.x * x.x - ph.y * x.y), (T)(ph.x * x.y + ph.y * x.x));
+  }
+  __syncthreads();
+  // convolution^H: zero-pad, inverse DFT, times conj(V), DFT
+  fft_inplace<T, kFftVPT>(buf, fN, twN, true);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmulc<T>(buf[k], V[k]);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fN, twN, false);
+  // theta-DFT^H: F^H_{m,m''} e^{+i m'' pi/M} placed on the length-M grid, inverse DFT
+  C<T> v[kFftVPT];
+#pragma unroll
+  for (int r = 0; r < kFftVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < M) {
+      const int mp = (k <= L - 1) ? k : k - M;
+      v[r] = cmulc<T>(buf[mp < 0 ? mp + N : mp], phase[mp + L - 1]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kFftVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < M) buf[k] = v[r];
+  }
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  // extension^H: G^H(t) = G~^H(t) + (-1)^(m+s) G~^H(2L-2-t) for t <= L-2
+  C<T>* out = Gt + (long long)b * L * M;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    C<T> a = buf[t];
+    if (t <= L - 2) {
+      const C<T> c = buf[2 * L - 2 - t];
+      a.x += (T)sg * c.x;
+      a.y += (T)sg * c.y;
+    }
+    out[(long long)t * M + im] = a;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ Gt,
+                                      double2* __restrict__ map, const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M;
+  const int t = blockIdx.x, b = blockIdx.y;
+  const C<T>* in = Gt + ((long long)b * L + t) * M;
+  double2* f = map + (long long)b * d.nmw;
+  if (t == L - 1) {  // pole: sum_p e^{-i s phi_p} (2pi/M) sum_m e^{i m phi_p} G^H = 2 pi G^H_s
+    if (threadIdx.x == 0) {
+      const int s = spin_of(spins, b);
+      const C<T> g = in[s + L - 1];
+      f[(long long)(L - 1) * M] = make_double2(2.0 * M_PI * (double)g.x, 2.0 * M_PI * (double)g.y);
+    }
+    return;
+  }
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const int m = (k <= L - 1) ? k : k - M;
+    buf[k] = in[m + L - 1];
+  }
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  const double sc = 2.0 * M_PI / M;
+  for (int p = threadIdx.x; p < M; p += blockDim.x) {
+    const double2 v = to64(buf[p]);
+    f[(long long)t * M + p] = make_double2(v.x * sc, v.y * sc);
+  }
+}
+
+// --------------------------------------------------------------------------
+// adjoint of the inverse: phi_inverse^H -> theta_inverse^H -> Wigner^H (run_wigner mode 0)
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM,
+                                      const double2* __restrict__ map, C<T>* __restrict__ Gt /* [B][M][L] */) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M;
+  const int t = blockIdx.x, b = blockIdx.y;
+  const double2* f = map + (long long)b * d.nmw;
+  C<T>* out = Gt + (long long)b * M * L;
+  if (t == L - 1) {  // only the phi = 0 sample of the pole ring is kept: F^H_m(pi) = x_pole
+    const C<T> xp = from64<T>(f[(long long)(L - 1) * M]);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) out[(long long)i * L + t] = xp;
+    return;
+  }
+  for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = from64<T>(f[(long long)t * M + p]);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const int m = i - (L - 1);
+    out[(long long)i * L + t] = buf[m < 0 ? m + M : m];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM,
+                                        const C<T>* __restrict__ phase, const C<T>* __restrict__ Gt,
+                                        double2* __restrict__ Gp, const int* __restrict__ spins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+  const int L = d.L, M = d.M;
+  const int im = blockIdx.x, b = blockIdx.y;
+  const int m = im - (L - 1);
+  const int s = spin_of(spins, b);
+  const double sg = (double)parity_sign(m + s);
+  const C<T>* g = Gt + ((long long)b * M + im) * L;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) buf[t] = (t < L) ? g[t] : mkc<T>(0, 0);
+  __syncthreads();
+  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  // F^H_mm' = e^{-i m' pi/M} DFT[m'], folded for the Wigner stage
+  double2* out = Gp + ((long long)b * M + im) * L;
+  for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
+    double2 a = to64(cmul<T>(buf[mp], phase[mp + L - 1]));
+    if (mp > 0) {
+      const double2 c = to64(cmul<T>(buf[M - mp], phase[-mp + L - 1]));
+      a.x += sg * c.x;
+      a.y += sg * c.y;
+    }
+    out[mp] = a;
+  }
+}
+
+// Pole sample of the forward adjoint, in FP64 for both precisions.  At
+// theta_{L-1} = pi the theta-DFT^H and convolution^H collapse to
+//   pole = (2 pi / M) sum_{m'} G^H_{s,m'} u(m'),  u(m') = sum_{m''} (-1)^{m''} conj(w(m''-m')),
+// and G^H_{s,-m'} = G^H_{s,m'} (the parity (-1)^(m+s) is +1 at m = s), so the sum
+// runs over m' >= 0 against u(m') + u(-m').  Evaluated this way the value does not
+// inherit the cancellation of the alternating sum over the FFT output.
+__global__ void k_pole_forward_adjoint(Dims d, const double2* __restrict__ Gp, const double2* __restrict__ upole,
+                                       double2* __restrict__ map, const int* __restrict__ spins) {
+  __shared__ double2 red[256];
+  const int b = blockIdx.x, L = d.L, M = d.M;
+  const int s = spin_of(spins, b);
+  const double2* w = Gp + ((long long)b * M + (s + L - 1)) * L;
+  double sr = 0.0, si = 0.0;
+  for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
+    const double2 x = w[mp], u = upole[mp];
+    sr += x.x * u.x - x.y * u.y;
+    si += x.x * u.y + x.y * u.x;
+  }
+  red[threadIdx.x] = make_double2(sr, si);
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      red[threadIdx.x].x += red[threadIdx.x + h].x;
+      red[threadIdx.x].y += red[threadIdx.x + h].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double2 ph = ipow(-2 * s);  // (-1)^s i^-(m+s) at m = s
+    if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+    const double c = 2.0 * M_PI / M;
+    const double2 v = red[0];
+    map[(long long)b * d.nmw + (long long)(L - 1) * M] =
+        make_double2(c * (ph.x * v.x - ph.y * v.y), c * (ph.x * v.y + ph.y * v.x));
+  }
+}
+
+template <typename T>
+int smem_bytes(int n) { return n * (int)sizeof(C<T>); }
+
+template <typename K>
+cudaError_t set_smem(K kernel, int bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaSuccess;
+}
+
+Dims dims_of(const mw_plan* p) {
+  Dims d;
+  d.L = p->L; d.M = p->M; d.N = p->N; d.B = p->B;
+  d.nmw = (long long)(p->L - 1) * p->M + 1;
+  return d;
+}
+
+int threads_for(int n) {
+  int t = (n + kFftVPT - 1) / kFftVPT;
+  t = ((t + 31) / 32) * 32;
+  return t < 32 ? 32 : t;
+}
+
+template <typename T>
+cudaError_t phi_forward_t(const mw_plan* p, const double2* map, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_phi_forward<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_phi_forward<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt, p->d_spins);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t theta_forward_t(const mw_plan* p, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->N);
+  cudaError_t e = set_smem(k_theta_forward<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_theta_forward<T><<<dim3(p->M, p->B), threads_for(p->N), sm, st>>>(
+      dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+      (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, p->d_Gp, p->d_spins);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t theta_inverse_t(const mw_plan* p, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_theta_inverse<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_theta_inverse<T><<<dim3(p->M, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t phi_inverse_t(const mw_plan* p, double2* map, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_phi_inverse<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_phi_inverse<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t theta_forward_adjoint_t(const mw_plan* p, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->N);
+  cudaError_t e = set_smem(k_theta_forward_adjoint<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_theta_forward_adjoint<T><<<dim3(p->M, p->B), threads_for(p->N), sm, st>>>(
+      dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+      (const C<T>*)p->d_V, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t phi_forward_adjoint_t(const mw_plan* p, double2* map, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_phi_forward_adjoint<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_phi_forward_adjoint<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_spins);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t phi_inverse_adjoint_t(const mw_plan* p, const double2* map, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_phi_inverse_adjoint<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_phi_inverse_adjoint<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t theta_inverse_adjoint_t(const mw_plan* p, cudaStream_t st) {
+  const int sm = smem_bytes<T>(p->M);
+  cudaError_t e = set_smem(k_theta_inverse_adjoint<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_theta_inverse_adjoint<T><<<dim3(p->M, p->B), threads_for(p->M), sm, st>>>(
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, (const C<T>*)p->d_Gt, p->d_Gp,
+      p->d_spins);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define DISPATCH(p, fn, ...) ((p)->prec == MW_PREC_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+cudaError_t launch_phi_forward(const mw_plan* p, const double2* map, cudaStream_t st) {
+  return DISPATCH(p, phi_forward_t, p, map, st);
+}
+cudaError_t launch_theta_forward(const mw_plan* p, cudaStream_t st) { return DISPATCH(p, theta_forward_t, p, st); }
+cudaError_t launch_theta_inverse(const mw_plan* p, cudaStream_t st) { return DISPATCH(p, theta_inverse_t, p, st); }
+cudaError_t launch_phi_inverse(const mw_plan* p, double2* map, cudaStream_t st) {
+  return DISPATCH(p, phi_inverse_t, p, map, st);
+}
+cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st) {
+  return DISPATCH(p, theta_forward_adjoint_t, p, st);
+}
+cudaError_t launch_phi_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st) {
+  return DISPATCH(p, phi_forward_adjoint_t, p, map, st);
+}
+cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st) {
+  return DISPATCH(p, phi_inverse_adjoint_t, p, map, st);
+}
+cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st) {
+  return DISPATCH(p, theta_inverse_adjoint_t, p, st);
+}
+cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st) {
+  k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_spins);
+  return cudaGetLastError();
+}

@@ -1,0 +1,168 @@
+"""Thin ctypes binding of libmw (include/mw.h).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+library.  If libmw.so is missing or cannot be loaded this module raises; there
+is no CPU fallback.  Tensors are complex128, on a CUDA device (the call is
+enqueued on torch's current stream of that device) or in host memory (the
+library stages them through its own device buffers).
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmw.so")
+
+MW_OK, MW_EINVAL, MW_ENOMEM, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = range(6)
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+_lib = None
+
+
+class MWError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}")
+
+
+def lib():
+    """Load libmw.so (raises OSError/RuntimeError if it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmw.so not built ({LIB_PATH}); run paper_1110_6298_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, c_int, c_uint, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
+        L.mw_plan_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, c_uint]
+        L.mw_plan_create_spins.argtypes = [ctypes.POINTER(vp), c_int, c_int, ctypes.POINTER(c_int), c_uint]
+        for name in ("mw_forward", "mw_inverse", "mw_forward_adjoint", "mw_inverse_adjoint"):
+            getattr(L, name).argtypes = [vp, vp, vp, vp]
+            getattr(L, name).restype = c_int
+        L.mw_plan_create.restype = c_int
+        L.mw_plan_create_spins.restype = c_int
+        L.mw_plan_destroy.argtypes = [vp]
+        L.mw_plan_destroy.restype = c_int
+        L.mw_status_string.argtypes = [c_int]
+        L.mw_status_string.restype = ctypes.c_char_p
+        L.mw_map_size.argtypes = [c_int]
+        L.mw_map_size.restype = c_size
+        L.mw_flm_size.argtypes = [c_int]
+        L.mw_flm_size.restype = c_size
+        L.mw_plan_workspace_bytes.argtypes = [vp]
+        L.mw_plan_workspace_bytes.restype = c_size
+        L.mw_plan_last_launches.argtypes = [vp]
+        L.mw_plan_last_launches.restype = c_int
+        L.mw_plan_set_timing.argtypes = [vp, c_int]
+        L.mw_plan_set_timing.restype = c_int
+        L.mw_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                          c_int]
+        L.mw_plan_stage_times.restype = c_int
+        _lib = L
+    return _lib
+
+
+def status_string(st):
+    return lib().mw_status_string(int(st)).decode()
+
+
+def map_size(L):
+    return int(lib().mw_map_size(int(L)))
+
+
+def flm_size(L):
+    return int(lib().mw_flm_size(int(L)))
+
+
+def _stream_of(t):
+    if t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """A transform plan: L, one spin per map (or one spin for all), precision."""
+
+    def __init__(self, L, spins, batch=None, precision="fp64"):
+        if isinstance(spins, int):
+            if batch is None:
+                batch = 1
+            spins = [spins] * int(batch)
+        spins = [int(s) for s in spins]
+        if batch is not None and int(batch) != len(spins):
+            raise ValueError("batch does not match len(spins)")
+        self.L, self.spins, self.batch = int(L), spins, len(spins)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * len(spins))(*spins)
+        st = lib().mw_plan_create_spins(ctypes.byref(h), self.L, self.batch, arr, PRECISIONS[precision])
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_create_spins")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mw_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self):
+        return int(lib().mw_plan_workspace_bytes(self._h))
+
+    @property
+    def last_launches(self):
+        return int(lib().mw_plan_last_launches(self._h))
+
+    STAGES = ("phi", "theta", "delta", "contract")
+
+    def set_timing(self, enable=True):
+        st = lib().mw_plan_set_timing(self._h, int(bool(enable)))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_set_timing")
+
+    def stage_times(self, reset=False):
+        """{stage: (milliseconds, launches)} accumulated since the last reset."""
+        ms = (ctypes.c_double * 4)()
+        nl = (ctypes.c_longlong * 4)()
+        st = lib().mw_plan_stage_times(self._h, ms, nl, int(bool(reset)))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_stage_times")
+        return {k: (ms[i], nl[i]) for i, k in enumerate(self.STAGES)}
+
+    def _call(self, name, x, n_in, n_out, out):
+        if x.dtype != torch.complex128:
+            raise TypeError("expected a complex128 tensor")
+        if x.numel() != self.batch * n_in:
+            raise ValueError(f"expected {self.batch}x{n_in} elements, got {tuple(x.shape)}")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty((self.batch, n_out), dtype=torch.complex128, device=x.device)
+        elif out.dtype != torch.complex128 or out.numel() != self.batch * n_out or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        st = getattr(lib(), name)(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  _stream_of(x))
+        if st != MW_OK:
+            raise MWError(st, name)
+        return out
+
+    def forward(self, maps, out=None):
+        return self._call("mw_forward", maps, map_size(self.L), flm_size(self.L), out)
+
+    def inverse(self, flm, out=None):
+        return self._call("mw_inverse", flm, flm_size(self.L), map_size(self.L), out)
+
+    def forward_adjoint(self, flm, out=None):
+        return self._call("mw_forward_adjoint", flm, flm_size(self.L), map_size(self.L), out)
+
+    def inverse_adjoint(self, maps, out=None):
+        return self._call("mw_inverse_adjoint", maps, map_size(self.L), flm_size(self.L), out)
