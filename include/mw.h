@@ -103,6 +103,12 @@ mw_status mw_inverse(mw_plan *plan, const void *flm_in, void *map_out, void *str
 mw_status mw_forward_adjoint(mw_plan *plan, const void *flm_in, void *map_out, void *stream);
 mw_status mw_inverse_adjoint(mw_plan *plan, const void *map_in, void *flm_out, void *stream);
 
+/* Wait for the plan's work on `stream` and report device-side errors: returns
+ * MW_ETIMEOUT (and clears the flag) if a tensor-core wait inside a kernel gave
+ * up since the last check -- the affected outputs are then invalid -- MW_ECUDA
+ * if the stream reports an error, MW_OK otherwise. */
+mw_status mw_plan_sync(mw_plan *plan, void *stream);
+
 /* Free a plan and its workspace.  NULL-safe.  Synchronises the device. */
 mw_status mw_plan_destroy(mw_plan *plan);
 

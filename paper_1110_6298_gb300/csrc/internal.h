@@ -17,7 +17,9 @@ struct FftDesc {
 // Maps that share a spin are contracted together against one Delta plane.
 // Each group holds at most kMaxGroupMaps maps (larger spin classes are split).
 constexpr int kMaxGroupMaps = 32;
-constexpr int kChunk = 64;  // Delta planes staged per contraction launch
+constexpr int kChunk = 64;         // Delta planes staged per FP64 contraction launch
+constexpr int kTcChunk = 128;      // Delta planes staged per tensor-core contraction launch
+constexpr int kTcGroupMaps = 8;    // maps per spin group on the tensor-core path (N = 4 x 8)
 
 struct SpinGroup {
   int s;
@@ -48,7 +50,10 @@ struct mw_plan {
   // workspace
   void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
   double2* d_Gp = nullptr;         // [B][M][L] folded G+_{m,m'} or F+_{m,m'}, m' >= 0
-  double* d_S = nullptr;           // [kChunk][LD][LD] staged integer Delta planes (quarter)
+  double* d_S = nullptr;           // FP64 path: [kChunk][LD][LD] staged integer Delta planes (quarter);
+                                   // mixed path: [2][LD][LD] ping-pong recursion state
+  float* d_S32 = nullptr;          // mixed path: [kTcChunk][LD][LD] FP32 copies of the integer planes
+  int* d_err = nullptr;            // device error word (tensor-core wait timeouts)
   double* d_H = nullptr;           // [LD][LD] half-integer plane
   int LD = 0;                      // plane row stride (L+1)
   double2* d_map_stage = nullptr;  // host-pointer staging
@@ -85,6 +90,8 @@ cudaError_t launch_phi_forward_adjoint(const mw_plan* p, double2* map, cudaStrea
 cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st);
 cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st);
 cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st);
+cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st);
+cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st);
 cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st);
 
 // Wigner stage: sweep l = 0..L-1 with Risbo's recursion and contract.

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc 
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
                                 const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
-                                const C<T>* __restrict__ V, const C<T>* __restrict__ Gt, double2* __restrict__ Gp,
+                                const C<T>* __restrict__ V, const C<T>* __restrict__ Gt, C<T>* __restrict__ Gp,
                                 const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
@@ -135,13 +135,13 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDes
   __syncthreads();
   fft_inplace<T, kFftVPT>(buf, fN, twN, false);
   // fold m' >= 0: G+_{m,0} = G_m0, G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'}
-  double2* out = Gp + ((long long)b * M + im) * L;
+  C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    double2 a = to64(buf[mp]);
+    C<T> a = buf[mp];
     if (mp > 0) {
-      const double2 c = to64(buf[N - mp]);
-      a.x += (double)sg * c.x;
-      a.y += (double)sg * c.y;
+      const C<T> c = buf[N - mp];
+      a.x += sg * c.x;
+      a.y += sg * c.y;
     }
     out[mp] = a;
   }
@@ -325,24 +325,24 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse_adjoint(Dims d, 
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM,
                                         const C<T>* __restrict__ phase, const C<T>* __restrict__ Gt,
-                                        double2* __restrict__ Gp, const int* __restrict__ spins) {
+                                        C<T>* __restrict__ Gp, const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int L = d.L, M = d.M;
   const int im = blockIdx.x, b = blockIdx.y;
   const int m = im - (L - 1);
   const int s = spin_of(spins, b);
-  const double sg = (double)parity_sign(m + s);
+  const T sg = (T)parity_sign(m + s);
   const C<T>* g = Gt + ((long long)b * M + im) * L;
   for (int t = threadIdx.x; t < M; t += blockDim.x) buf[t] = (t < L) ? g[t] : mkc<T>(0, 0);
   __syncthreads();
   fft_inplace<T, kFftVPT>(buf, fM, twM, false);
   // F^H_mm' = e^{-i m' pi/M} DFT[m'], folded for the Wigner stage
-  double2* out = Gp + ((long long)b * M + im) * L;
+  C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    double2 a = to64(cmul<T>(buf[mp], phase[mp + L - 1]));
+    C<T> a = cmul<T>(buf[mp], phase[mp + L - 1]);
     if (mp > 0) {
-      const double2 c = to64(cmul<T>(buf[M - mp], phase[-mp + L - 1]));
+      const C<T> c = cmul<T>(buf[M - mp], phase[-mp + L - 1]);
       a.x += sg * c.x;
       a.y += sg * c.y;
     }
@@ -425,7 +425,7 @@ cudaError_t theta_forward_t(const mw_plan* p, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_theta_forward<T><<<dim3(p->M, p->B), threads_for(p->N), sm, st>>>(
       dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
-      (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, p->d_Gp, p->d_spins);
+      (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
@@ -480,7 +480,7 @@ cudaError_t theta_inverse_adjoint_t(const mw_plan* p, cudaStream_t st) {
   cudaError_t e = set_smem(k_theta_inverse_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
   k_theta_inverse_adjoint<T><<<dim3(p->M, p->B), threads_for(p->M), sm, st>>>(
-      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, (const C<T>*)p->d_Gt, p->d_Gp,
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp,
       p->d_spins);
   return cudaGetLastError();
 }

@@ -1,0 +1,330 @@
+// kernels_tc.cu -- split-precision Delta contractions on the tensor cores (tcgen05).
+//
+// For one chunk of 128 consecutive l and one |m| = am, the forward sum of
+// Eq. (flm_wig) over m' >= 0 (the +-m' fold is already in G+) is a GEMM
+//   out[l, n] = sum_{m'} A[l, m'] B[n, m'],   A[l, m'] = Delta^l_{m',am} Delta^l_{m',-s}
+// with n running over (map, re/im) for m = +am and, for m = -am, over the same
+// maps with B multiplied by (-1)^{m'} and the result by (-1)^l, because
+// Delta_{m',-am} = (-1)^(l+m') Delta_{m',am} (Eq. wignerd_sym2 at pi/2).  So one
+// A tile serves both signs of m and N = 4 x (maps of the spin group) <= 32.
+// The inverse sum of Eq. (Fmm) is the transposed GEMM, rows m', K = l.
+//
+// Precision: A and B are formed in FP32 and split into three BF16 parts
+// (x = hi + mid + lo); six products hi.hi, hi.mid, mid.hi, hi.lo, mid.mid,
+// lo.hi are formed on the tensor cores.  A single K = 16 MMA into a fresh
+// accumulator errs by about 2^-24 of the sum of its |products| (measured on
+// this part), but every further MMA accumulated into the same FP32 accumulator
+// adds an error of that size relative to the growing partial sum.  So the main
+// hi.hi product of each K step goes to a fresh TMEM slot of its own, while the
+// correction products (2^-8 and 2^-16 smaller) accumulate in two more slots;
+// the six slots of a 64-wide K tile are then summed on the CUDA cores in
+// float-float (TwoSum) accumulators, which also carry the sum across K tiles,
+// and converted to FP64 at the end.
+//
+// Layout: operands in shared memory in the no-swizzle K-major core-matrix
+// layout, written by all threads; thread 0 issues the MMAs and commits them to
+// an mbarrier that every thread waits on (bounded; a timeout sets the plan's
+// error word and skips the accumulator read); warp w then reads TMEM lanes
+// 32w..32w+31 (= rows of the tile).
+#include <cmath>
+
+#include "internal.h"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int kKTile = 64;            // K per operand tile (4 MMAs of K = 16)
+constexpr int kN = 4 * kTcGroupMaps;  // 32 accumulator columns
+constexpr int kATile = 128 * kKTile * 2;  // bytes of one bf16 A split (16 KB)
+constexpr int kBTile = kN * kKTile * 2;   // bytes of one bf16 B split (4 KB)
+constexpr int kSmemUsed = 3 * kATile + 3 * kBTile + 64;
+// Requested dynamic shared memory: at least 80 KB so that no more than two
+// blocks share an SM, which keeps 2 x kTmemCols <= 512 TMEM columns.
+constexpr int kSmem = kSmemUsed > 80 * 1024 ? kSmemUsed : 80 * 1024;
+constexpr int kSlots = 6;               // TMEM accumulator slots of kN columns
+constexpr uint32_t kTmemCols = 256;     // >= kSlots * kN, power of two
+constexpr uint32_t kMaxPolls = 1u << 26;
+// split pairs (A part, B part) of the six products, largest first, and the
+// TMEM slot each goes to (slot ks for hi.hi of K step ks, 4 and 5 for the
+// two correction classes)
+__device__ __forceinline__ int split_a(int p) { return (0x210100 >> (4 * p)) & 0xF; }  // 0,0,1,0,1,2
+__device__ __forceinline__ int split_b(int p) { return (0x012010 >> (4 * p)) & 0xF; }  // 0,1,0,2,1,0
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ void store_split(unsigned char* base, int tile_bytes, int off, float x) {
+  __nv_bfloat16 h, m, l;
+  umma::split3(x, h, m, l);
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(base + tile_bytes + off) = m;
+  *reinterpret_cast<__nv_bfloat16*>(base + 2 * tile_bytes + off) = l;
+}
+
+// Issue the 4 K steps x 6 split products of one 64-wide K tile into the six
+// accumulator slots (every slot starts fresh in each tile).
+__device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t sb, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < kKTile / 16; ++ks) {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const uint64_t ad = umma::smem_desc(sa + split_a(p) * kATile + ks * 256, 128, (kKTile / 8) * 128);
+      const uint64_t bd = umma::smem_desc(sb + split_b(p) * kBTile + ks * 256, 128, (kKTile / 8) * 128);
+      const int slot = (p == 0) ? ks : (p < 3 ? 4 : 5);
+      const int acc = (p == 0) ? 0 : ((ks == 0 && (p == 1 || p == 3)) ? 0 : 1);
+      umma::mma_bf16(tmem + (uint32_t)(slot * kN), ad, bd, idesc, acc);
+    }
+  }
+}
+
+// Add the six slots of this warp's 32 rows into float-float accumulators.
+__device__ __forceinline__ void drain_slots(uint32_t tmem, int warp, float* hi, float* lo) {
+#pragma unroll
+  for (int slot = 0; slot < kSlots; ++slot) {
+#pragma unroll
+    for (int c0 = 0; c0 < kN; c0 += 16) {
+      float v[16];
+      umma::ld_32x32b_x16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(slot * kN + c0), v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j]);
+    }
+  }
+}
+
+__device__ __forceinline__ void sync_all() {
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+}
+
+// Every thread waits (bounded) for the committed MMAs; the result is made
+// block-uniform so that the warp-collective TMEM loads are never divergent.
+__device__ __forceinline__ bool wait_all(uint64_t* mbar, uint32_t phase) {
+  const bool w = umma::mbar_wait(mbar, phase, kMaxPolls);
+  umma::fence_before();
+  const int all = __syncthreads_and(w ? 1 : 0);
+  umma::fence_after();
+  return all != 0;
+}
+
+// ---------------------------------------------------------------------------
+// forward: f_lm for l in [l0, l1), both signs of m = +-am, every spin group
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
+                                                    int l1, const SpinGroup* __restrict__ groups, int ng,
+                                                    const float2* __restrict__ Gp, double2* __restrict__ flm,
+                                                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + 3 * kATile;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 3 * kATile + 3 * kBTile);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int am = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) umma::mbar_init(mbar, 1);
+  if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
+  sync_all();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = umma::idesc_bf16_f32(128, kN);
+  const size_t plane = (size_t)LD * LD;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int row = warp * 32 + lane;  // TMEM lane = tile row = l - l0
+  for (int gi = 0; gi < ng; ++gi) {
+    const SpinGroup& g = groups[gi];
+    const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
+    const int lstart = max(max(l0, am), as);
+    float ahi[kN], alo[kN];
+#pragma unroll
+    for (int j = 0; j < kN; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
+    if (lstart < l1) {
+      for (int mp0 = 0; mp0 < l1; mp0 += kKTile) {
+        for (int idx = tid; idx < 128 * kKTile; idx += 128) {
+          const int r = idx / kKTile, k = idx % kKTile;
+          const int l = l0 + r, mp = mp0 + k;
+          float x = 0.f;
+          if (l >= lstart && l < l1 && mp <= l) {
+            const float* P = S + (size_t)(l - l0) * plane;
+            x = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
+            if ((am + as + (s > 0 ? l + mp : 0)) & 1) x = -x;
+          }
+          store_split(sA, kATile, umma::tile_off(r, k, kKTile / 8), x);
+        }
+        for (int idx = tid; idx < kN * kKTile; idx += 128) {
+          const int n = idx / kKTile, k = idx % kKTile;
+          const int j = n >> 1, mp = mp0 + k;
+          float x = 0.f;
+          if (j < 2 * nb && mp < L) {
+            const bool neg = j >= nb;
+            if (!(neg && am == 0)) {
+              const int b = g.maps[neg ? j - nb : j];
+              const float2 v = Gp[((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp];
+              x = (n & 1) ? v.y : v.x;
+              if (neg && (mp & 1)) x = -x;
+            }
+          }
+          store_split(sB, kBTile, umma::tile_off(n, k, kKTile / 8), x);
+        }
+        umma::fence_proxy_async();
+        sync_all();
+        if (tid == 0) {
+          issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+          umma::commit(mbar);
+        }
+        const bool w = wait_all(mbar, phase);
+        phase ^= 1u;
+        ok = ok && w;
+        if (w) drain_slots(tmem, warp, ahi, alo);
+        sync_all();
+      }
+    }
+    // epilogue: times (-1)^s i^(m+s) N_l (and (-1)^l for m = -am)
+    const int l = l0 + row;
+    if (l >= am && l >= l0 && l < l1) {
+      const double nl = ((s & 1) ? -1.0 : 1.0) * sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+#pragma unroll
+      for (int j = 0; j < 2 * kTcGroupMaps; ++j) {
+        if (j >= 2 * nb) continue;
+        const bool neg = j >= nb;
+        if (neg && am == 0) continue;
+        const int m = neg ? -am : am;
+        double2 o = make_double2(0.0, 0.0);
+        if (l >= as) {
+          double ar = (double)ahi[2 * j] + (double)alo[2 * j], ai = (double)ahi[2 * j + 1] + (double)alo[2 * j + 1];
+          if (neg && (l & 1)) { ar = -ar; ai = -ai; }
+          const int r4 = (m + s) & 3;
+          const double pr = (r4 == 0) ? 1.0 : (r4 == 2 ? -1.0 : 0.0);
+          const double pi_ = (r4 == 1) ? 1.0 : (r4 == 3 ? -1.0 : 0.0);
+          o.x = nl * (pr * ar - pi_ * ai);
+          o.y = nl * (pr * ai + pi_ * ar);
+        }
+        flm[(size_t)g.maps[neg ? j - nb : j] * L * L + (size_t)l * l + l + m] = o;
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  sync_all();
+  if (warp == 0) umma::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// inverse: F+_{+-am, m'} += sum_{l in [l0,l1)} N_l Delta^l_{m',am} Delta^l_{m',-s} f_{l,+-am}
+// one block per (am, 128-row tile of m', spin group)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
+                                                    int l1, const SpinGroup* __restrict__ groups,
+                                                    const double2* __restrict__ flm, double2* __restrict__ Fp,
+                                                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + 3 * kATile;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 3 * kATile + 3 * kBTile);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int am = blockIdx.x, mp0 = blockIdx.y * 128;
+  const SpinGroup& g = groups[blockIdx.z];
+  const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
+  const int lstart = max(max(l0, am), as);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (lstart >= l1 || mp0 >= l1) return;  // block-uniform: nothing to add
+  if (tid == 0) umma::mbar_init(mbar, 1);
+  if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
+  sync_all();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = umma::idesc_bf16_f32(128, kN);
+  const size_t plane = (size_t)LD * LD;
+  uint32_t phase = 0;
+  bool ok = true;
+  float ahi[kN], alo[kN];
+#pragma unroll
+  for (int j = 0; j < kN; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
+  for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
+    const int lb = l0 + kt * kKTile;
+    for (int idx = tid; idx < 128 * kKTile; idx += 128) {
+      const int r = idx % 128, k = idx / 128;
+      const int l = lb + k, mp = mp0 + r;
+      float x = 0.f;
+      if (l >= lstart && l < l1 && mp <= l) {
+        const float* P = S + (size_t)(l - l0) * plane;
+        x = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
+        if ((am + as + (s > 0 ? l + mp : 0)) & 1) x = -x;
+      }
+      store_split(sA, kATile, umma::tile_off(r, k, kKTile / 8), x);
+    }
+    for (int idx = tid; idx < kN * kKTile; idx += 128) {
+      const int n = idx / kKTile, k = idx % kKTile;
+      const int j = n >> 1, l = lb + k;
+      float x = 0.f;
+      if (j < 2 * nb && l >= lstart && l < l1) {
+        const bool neg = j >= nb;
+        if (!(neg && am == 0)) {
+          const int b = g.maps[neg ? j - nb : j];
+          const double2 f = flm[(size_t)b * L * L + (size_t)l * l + l + (neg ? -am : am)];
+          const double nl = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+          double v = ((n & 1) ? f.y : f.x) * nl;
+          if (neg && (l & 1)) v = -v;
+          x = (float)v;
+        }
+      }
+      store_split(sB, kBTile, umma::tile_off(n, k, kKTile / 8), x);
+    }
+    umma::fence_proxy_async();
+    sync_all();
+    if (tid == 0) {
+      issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+      umma::commit(mbar);
+    }
+    const bool w = wait_all(mbar, phase);
+    phase ^= 1u;
+    ok = ok && w;
+    if (!ok) break;
+    drain_slots(tmem, warp, ahi, alo);
+    sync_all();
+  }
+  // epilogue: add the chunk's sum into the FP64 accumulator F+
+  const int mp = mp0 + warp * 32 + lane;
+  if (ok) {
+    if (mp < L && mp < l1) {
+#pragma unroll
+      for (int j = 0; j < 2 * kTcGroupMaps; ++j) {
+        if (j >= 2 * nb) continue;
+        const bool neg = j >= nb;
+        if (neg && am == 0) continue;
+        const int b = g.maps[neg ? j - nb : j];
+        double2* dst = Fp + ((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp;
+        double re = (double)ahi[2 * j] + (double)alo[2 * j], im = (double)ahi[2 * j + 1] + (double)alo[2 * j + 1];
+        if (neg && (mp & 1)) { re = -re; im = -im; }
+        double2 cur = *dst;
+        cur.x += re;
+        cur.y += im;
+        *dst = cur;
+      }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  sync_all();
+  if (warp == 0) umma::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  k_tc_forward<<<l1, 128, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
+                                       reinterpret_cast<const float2*>(p->d_Gp), flm, p->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(l1, (l1 + 127) / 128, (unsigned)p->groups.size());
+  k_tc_inverse<<<grid, 128, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, flm,
+                                         reinterpret_cast<double2*>(p->d_Gp), p->d_err);
+  return cudaGetLastError();
+}

@@ -32,7 +32,7 @@ __device__ __forceinline__ double sgn_pow(int k) { return (k & 1) ? -1.0 : 1.0; 
 
 // new plane 2j' = two_jp from old plane (j = j' - 1/2)
 __global__ void k_risbo_half(const double* __restrict__ d, double* __restrict__ e, int two_jp, int LD,
-                             const double* __restrict__ sq, double scale) {
+                             const double* __restrict__ sq, double scale, float* __restrict__ stage) {
   const int odd = two_jp & 1;                // j' half-integer
   const int nnew = odd ? (two_jp + 1) / 2 : two_jp / 2 + 1;
   const int nold = (two_jp + 1) / 2;
@@ -64,10 +64,15 @@ __global__ void k_risbo_half(const double* __restrict__ d, double* __restrict__ 
   };
   const double dpp = at(ip, jp), dmp = at(im, jp), dpm = at(ip, jm), dmm = at(im, jm);
   const double v = cmn * (cmm * dpp - cpm * dmp) + cpn * (cmm * dpm + cpm * dmm);
-  e[(size_t)a * LD + b] = scale * v;
+  const double out = scale * v;
+  e[(size_t)a * LD + b] = out;
+  if (stage) stage[(size_t)a * LD + b] = (float)out;  // FP32 copy for the tensor-core contraction
 }
 
-__global__ void k_plane_init(double* S) { S[0] = 1.0; }
+__global__ void k_plane_init(double* S, float* S32) {
+  S[0] = 1.0;
+  if (S32) S32[0] = 1.0f;
+}
 
 // Forward contraction for planes l in [l0, l1) stored at slots l % kChunk:
 //   f_lm = (-1)^s i^(m+s) N_l sum_{m'=0}^{l} K_m[l,m'] G+_{m,m'},
@@ -210,8 +215,10 @@ __global__ void k_contract_inverse(const double* __restrict__ S, int LD, int L, 
 
 }  // namespace
 
-cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
-                       int* launches) {
+namespace {
+
+cudaError_t run_wigner_fp64(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
+                            int* launches) {
   const int L = p->L, M = p->M, LD = p->LD;
   const int ng = (int)p->groups.size();
   int nl = 0;
@@ -220,7 +227,7 @@ cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm
     e = cudaMemsetAsync(p->d_Gp, 0, sizeof(double2) * (size_t)p->B * M * L, st);
     if (e != cudaSuccess) return e;
   }
-  k_plane_init<<<1, 1, 0, st>>>(p->d_S);
+  k_plane_init<<<1, 1, 0, st>>>(p->d_S, nullptr);
   ++nl;
   for (int l0 = 0; l0 < L; l0 += kChunk) {
     const int l1 = (l0 + kChunk < L) ? l0 + kChunk : L;
@@ -237,7 +244,7 @@ cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm
         const dim3 grd((nnew + 31) / 32, (nnew + 7) / 8);
         const double scale = 1.0 / (sqrt(2.0) * (double)two_jp);
         k_risbo_half<<<grd, blk, 0, st>>>(h == 0 ? prev : p->d_H, h == 0 ? p->d_H : cur, two_jp, LD, p->d_sqrt,
-                                          scale);
+                                          scale, nullptr);
         ++nd;
       }
     }
@@ -257,4 +264,56 @@ cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm
   }
   if (launches) *launches += nl;
   return cudaGetLastError();
+}
+
+// Mixed path: FP64 recursion state in two ping-pong planes, FP32 copies of the
+// integer planes of a 128-plane chunk for the tensor-core contraction.
+cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
+                             int* launches) {
+  const int L = p->L, M = p->M, LD = p->LD;
+  const size_t plane = (size_t)LD * LD;
+  int nl = 0;
+  cudaError_t e;
+  if (mode == 1) {
+    e = cudaMemsetAsync(p->d_Gp, 0, sizeof(double2) * (size_t)p->B * M * L, st);
+    if (e != cudaSuccess) return e;
+  }
+  k_plane_init<<<1, 1, 0, st>>>(p->d_S, p->d_S32);
+  ++nl;
+  for (int l0 = 0; l0 < L; l0 += kTcChunk) {
+    const int l1 = (l0 + kTcChunk < L) ? l0 + kTcChunk : L;
+    StageSpan span_d(p, MW_STAGE_DELTA, st);
+    int nd = 0;
+    for (int l = (l0 == 0 ? 1 : l0); l < l1; ++l) {
+      const double* prev = p->d_S + (size_t)((l - 1) & 1) * plane;
+      double* cur = p->d_S + (size_t)(l & 1) * plane;
+      for (int h = 0; h < 2; ++h) {
+        const int two_jp = 2 * l - 1 + h;
+        const int nnew = (two_jp & 1) ? (two_jp + 1) / 2 : two_jp / 2 + 1;
+        const dim3 blk(32, 8);
+        const dim3 grd((nnew + 31) / 32, (nnew + 7) / 8);
+        const double scale = 1.0 / (sqrt(2.0) * (double)two_jp);
+        k_risbo_half<<<grd, blk, 0, st>>>(h == 0 ? prev : p->d_H, h == 0 ? p->d_H : cur, two_jp, LD, p->d_sqrt,
+                                          scale, h == 0 ? nullptr : p->d_S32 + (size_t)(l - l0) * plane);
+        ++nd;
+      }
+    }
+    span_d.end(nd);
+    nl += nd;
+    StageSpan span_c(p, MW_STAGE_CONTRACT, st);
+    e = (mode == 0) ? launch_tc_forward(p, l0, l1, flm_out, st) : launch_tc_inverse(p, l0, l1, flm_in, st);
+    span_c.end(1);
+    ++nl;
+    if (e != cudaSuccess) return e;
+  }
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
+                       int* launches) {
+  return p->prec == MW_PREC_FP64 ? run_wigner_fp64(p, mode, flm_in, flm_out, st, launches)
+                                 : run_wigner_mixed(p, mode, flm_in, flm_out, st, launches);
 }

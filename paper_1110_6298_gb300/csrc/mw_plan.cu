@@ -65,7 +65,7 @@ cudaError_t upload_complex(const std::vector<double>& re, const std::vector<doub
 void free_plan(mw_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
-                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage};
+                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -103,11 +103,13 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   p->spins.assign(spins, spins + B);
   if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
 
-  // spin groups (order of first appearance, at most kMaxGroupMaps maps each)
+  // spin groups (order of first appearance; at most kMaxGroupMaps maps each,
+  // kTcGroupMaps on the tensor-core path)
+  const int gmax = prec == MW_PREC_MIXED ? kTcGroupMaps : kMaxGroupMaps;
   for (int b = 0; b < B; ++b) {
     SpinGroup* g = nullptr;
     for (auto& h : p->groups)
-      if (h.s == spins[b] && h.nb < kMaxGroupMaps) g = &h;
+      if (h.s == spins[b] && h.nb < gmax) g = &h;
     if (!g) {
       SpinGroup ng{};
       ng.s = spins[b];
@@ -203,8 +205,12 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   const size_t fsz = dbl ? sizeof(double2) : sizeof(float2);
   alloc(&p->d_Gt, fsz * (size_t)B * M * L);
   alloc((void**)&p->d_Gp, sizeof(double2) * (size_t)B * M * L);
-  alloc((void**)&p->d_S, sizeof(double) * (size_t)kChunk * p->LD * p->LD);
-  alloc((void**)&p->d_H, sizeof(double) * (size_t)p->LD * p->LD);
+  const size_t plane = (size_t)p->LD * p->LD;
+  alloc((void**)&p->d_S, sizeof(double) * (dbl ? (size_t)kChunk : 2) * plane);
+  alloc((void**)&p->d_H, sizeof(double) * plane);
+  if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)kTcChunk * plane);
+  alloc((void**)&p->d_err, sizeof(int));
+  if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
   if (e != cudaSuccess) {
     const mw_status st = from_cuda(e);
     cudaGetLastError();
@@ -333,6 +339,20 @@ void StageSpan::end(int launches) {
 }
 
 extern "C" {
+
+mw_status mw_plan_sync(mw_plan* plan, void* stream) {
+  if (!plan) return MW_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  int flag = 0;
+  e = cudaMemcpy(&flag, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (flag) {
+    cudaMemset(plan->d_err, 0, sizeof(int));
+    return MW_ETIMEOUT;
+  }
+  return MW_OK;
+}
 
 mw_status mw_plan_set_timing(mw_plan* plan, int enable) {
   if (!plan) return MW_EINVAL;

@@ -53,6 +53,8 @@ def lib():
         L.mw_plan_workspace_bytes.restype = c_size
         L.mw_plan_last_launches.argtypes = [vp]
         L.mw_plan_last_launches.restype = c_int
+        L.mw_plan_sync.argtypes = [vp, vp]
+        L.mw_plan_sync.restype = c_int
         L.mw_plan_set_timing.argtypes = [vp, c_int]
         L.mw_plan_set_timing.restype = c_int
         L.mw_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -122,6 +124,14 @@ class Plan:
     @property
     def last_launches(self):
         return int(lib().mw_plan_last_launches(self._h))
+
+    def sync(self, stream=None):
+        """Wait for this plan's work and raise MWError on a device-side timeout."""
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        st = lib().mw_plan_sync(self._h, ctypes.c_void_p(stream))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_sync")
 
     STAGES = ("phi", "theta", "delta", "contract")
 
