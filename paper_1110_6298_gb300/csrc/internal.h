@@ -46,6 +46,9 @@ struct mw_plan {
   void* d_V = nullptr;             // DFT_N of the reflected weights, pre-scaled by 1/(N M)
   double* d_sqrt = nullptr;        // sqrt(k), k = 0..2L+2
   double2* d_upole = nullptr;      // u(m') + u(-m') (m' > 0), u(0): pole row of the forward adjoint
+  double* d_rscale = nullptr;      // 1 / (sqrt2 * two_jp) for the Risbo half step to plane two_jp / 2
+  double* d_nl = nullptr;          // sqrt((2l+1)/(4 pi)), l < L
+  float2* d_flmf = nullptr;        // mixed path: N_l f_lm in FP32 (input of the inverse contraction)
 
   // workspace
   void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
@@ -53,7 +56,9 @@ struct mw_plan {
   double* d_S = nullptr;           // FP64 path: [kChunk][LD][LD] staged integer Delta planes (quarter);
                                    // mixed path: [2][LD][LD] ping-pong recursion state
   float* d_S32 = nullptr;          // mixed path: [kTcChunk][LD][LD] FP32 copies of the integer planes
-  int* d_err = nullptr;            // device error word (tensor-core wait timeouts)
+  int* d_err = nullptr;            // device error word (bit 0: tensor-core wait, bit 1: grid barrier)
+  unsigned* d_bar = nullptr;       // grid-barrier counter of the persistent Risbo kernel
+  int risbo_grid = 0;              // co-resident blocks of the persistent Risbo kernel
   double* d_H = nullptr;           // [LD][LD] half-integer plane
   int LD = 0;                      // plane row stride (L+1)
   double2* d_map_stage = nullptr;  // host-pointer staging
@@ -91,10 +96,13 @@ cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st);
 cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st);
 cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st);
 cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st);
-cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st);
+cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const float2* flmf, cudaStream_t st);
+cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t st);
 cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st);
 
 // Wigner stage: sweep l = 0..L-1 with Risbo's recursion and contract.
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
+int risbo_blocks_per_sm();
+
 cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out,
                        cudaStream_t st, int* launches);

@@ -54,6 +54,17 @@ __device__ __forceinline__ double2 ipow(int k) {
   return make_double2(r == 0 ? 1.0 : (r == 2 ? -1.0 : 0.0), r == 1 ? 1.0 : (r == 3 ? -1.0 : 0.0));
 }
 
+// x * i^k, exact (swaps and sign changes only)
+template <typename T>
+__device__ __forceinline__ C<T> mul_ipow(C<T> x, int k) {
+  switch (k & 3) {
+    case 0: return x;
+    case 1: return mkc<T>(-x.y, x.x);
+    case 2: return mkc<T>(-x.x, -x.y);
+    default: return mkc<T>(x.y, -x.x);
+  }
+}
+
 struct Dims {
   int L, M, N, B;
   long long nmw;  // samples per map
@@ -160,19 +171,16 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDes
   const int im = blockIdx.x, b = blockIdx.y;
   const int m = im - (L - 1);
   const int s = spin_of(spins, b);
-  const double sg = (double)parity_sign(m + s);
-  // (-1)^s i^-(m+s)
-  double2 ph = ipow(-(m + s));
-  if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+  // (-1)^s i^-(m+s) and the unfold sign (-1)^(m+s) are applied exactly in T
+  const int ph = -(m + s) + ((s & 1) ? 2 : 0);
   const double2* in = Gp + ((long long)b * M + im) * L;
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     const int mp = (k <= L - 1) ? k : k - M;  // slot of m' in the length-M DFT
     const int a = mp < 0 ? -mp : mp;
-    double2 x = in[a];
-    if (mp < 0) { x.x *= sg; x.y *= sg; }
-    const double2 y = make_double2(ph.x * x.x - ph.y * x.y, ph.x * x.y + ph.y * x.x);
+    const int q = ph + ((mp < 0 && ((m + s) & 1)) ? 2 : 0);
+    const C<T> y = mul_ipow<T>(from64<T>(in[a]), q);
     // times e^{+i m' pi / M} = conj(phase)
-    buf[k] = cmulc<T>(mkc<T>((T)y.x, (T)y.y), phase[mp + L - 1]);
+    buf[k] = cmulc<T>(y, phase[mp + L - 1]);
   }
   __syncthreads();
   fft_inplace<T, kFftVPT>(buf, fM, twM, true);
@@ -216,18 +224,16 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d
   const int im = blockIdx.x, b = blockIdx.y;
   const int m = im - (L - 1);
   const int s = spin_of(spins, b);
-  const double sg = (double)parity_sign(m + s);
-  double2 ph = ipow(-(m + s));  // conj of (-1)^s i^(m+s)
-  if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
+  const T sg = (T)parity_sign(m + s);
+  const int ph = -(m + s) + ((s & 1) ? 2 : 0);  // conj of (-1)^s i^(m+s), exact
   const double2* in = Gp + ((long long)b * M + im) * L;
   // G^H_mm' for |m'| <= L-1, zero-padded to N
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
     if (mp == 0x7fffffff) { buf[k] = mkc<T>(0, 0); continue; }
     const int a = mp < 0 ? -mp : mp;
-    double2 x = in[a];
-    if (mp < 0) { x.x *= sg; x.y *= sg; }
-    buf[k] = mkc<T>((T)(ph.x * x.x - ph.y * x.y), (T)(ph.x * x.y + ph.y * x.x));
+    const int q = ph + ((mp < 0 && ((m + s) & 1)) ? 2 : 0);
+    buf[k] = mul_ipow<T>(from64<T>(in[a]), q);
   }
   __syncthreads();
   // convolution^H: zero-pad, inverse DFT, times conj(V), DFT
@@ -278,8 +284,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, 
   if (t == L - 1) {  // pole: sum_p e^{-i s phi_p} (2pi/M) sum_m e^{i m phi_p} G^H = 2 pi G^H_s
     if (threadIdx.x == 0) {
       const int s = spin_of(spins, b);
-      const C<T> g = in[s + L - 1];
-      f[(long long)(L - 1) * M] = make_double2(2.0 * M_PI * (double)g.x, 2.0 * M_PI * (double)g.y);
+      f[(long long)(L - 1) * M] = to64(cscale<T>(in[s + L - 1], (T)(2.0 * M_PI)));
     }
     return;
   }
@@ -289,11 +294,8 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, 
   }
   __syncthreads();
   fft_inplace<T, kFftVPT>(buf, fM, twM, true);
-  const double sc = 2.0 * M_PI / M;
-  for (int p = threadIdx.x; p < M; p += blockDim.x) {
-    const double2 v = to64(buf[p]);
-    f[(long long)t * M + p] = make_double2(v.x * sc, v.y * sc);
-  }
+  const T sc = (T)(2.0 * M_PI / M);
+  for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(cscale<T>(buf[p], sc));
 }
 
 // --------------------------------------------------------------------------

@@ -58,14 +58,6 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
   lo += err;
 }
 
-__device__ __forceinline__ void store_split(unsigned char* base, int tile_bytes, int off, float x) {
-  __nv_bfloat16 h, m, l;
-  umma::split3(x, h, m, l);
-  *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(base + tile_bytes + off) = m;
-  *reinterpret_cast<__nv_bfloat16*>(base + 2 * tile_bytes + off) = l;
-}
-
 // Issue the 4 K steps x 6 split products of one 64-wide K tile into the six
 // accumulator slots (every slot starts fresh in each tile).
 __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t sb, uint32_t idesc) {
@@ -82,17 +74,15 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t 
   }
 }
 
-// Add the six slots of this warp's 32 rows into float-float accumulators.
-__device__ __forceinline__ void drain_slots(uint32_t tmem, int warp, float* hi, float* lo) {
+// Add the six slots into float-float accumulators: warp quadrant q owns TMEM
+// lanes (tile rows) 32q..32q+31, half h owns columns 16h..16h+15 of each slot.
+__device__ __forceinline__ void drain_half(uint32_t tmem, int quad, int half, float* hi, float* lo) {
 #pragma unroll
   for (int slot = 0; slot < kSlots; ++slot) {
+    float v[16];
+    umma::ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * kN + 16 * half), v);
 #pragma unroll
-    for (int c0 = 0; c0 < kN; c0 += 16) {
-      float v[16];
-      umma::ld_32x32b_x16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(slot * kN + c0), v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j]);
-    }
+    for (int j = 0; j < 16; ++j) two_sum_acc(hi[j], lo[j], v[j]);
   }
 }
 
@@ -112,13 +102,57 @@ __device__ __forceinline__ bool wait_all(uint64_t* mbar, uint32_t phase) {
   return all != 0;
 }
 
+constexpr int kThreads = 256;  // 8 warps: warp w drains TMEM lanes 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15
+
+// 8 FP32 values -> three 16-byte rows of bf16 (hi, mid, lo) at byte offset off of each split tile
+__device__ __forceinline__ void store_split8(unsigned char* base, int tile_bytes, int off, const float* x) {
+  uint32_t h[4], m[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+    umma::split3(x[2 * i], h0, m0, l0);
+    umma::split3(x[2 * i + 1], h1, m1, l1);
+    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    m[i] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(base + tile_bytes + off) = make_uint4(m[0], m[1], m[2], m[3]);
+  *reinterpret_cast<uint4*>(base + 2 * tile_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// 8 consecutive floats from a 32-byte aligned address
+__device__ __forceinline__ void load8(const float* __restrict__ p, float* v) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Kernel values A = Delta_{m',am} Delta_{m',-s} (sign folded) for 8 consecutive m'
+// of plane P; entries with m' > l are zero.
+__device__ __forceinline__ void kernel8(const float* __restrict__ P, int LD, int am, int as, int s, int l, int mp,
+                                        float* x) {
+  float a[8], w[8];
+  load8(P + (size_t)am * LD + mp, a);
+  load8(P + (size_t)as * LD + mp, w);
+  const int base = am + as + (s > 0 ? l + mp : 0);
+  const bool alt = s > 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float v = a[i] * w[i];
+    if ((base + (alt ? i : 0)) & 1) v = -v;
+    x[i] = (mp + i <= l) ? v : 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // forward: f_lm for l in [l0, l1), both signs of m = +-am, every spin group
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
-                                                    int l1, const SpinGroup* __restrict__ groups, int ng,
-                                                    const float2* __restrict__ Gp, double2* __restrict__ flm,
-                                                    int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
+                                                         int l1, const SpinGroup* __restrict__ groups, int ng,
+                                                         const float2* __restrict__ Gp,
+                                                         const double* __restrict__ nltab,
+                                                         double2* __restrict__ flm, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
   unsigned char* sB = smem + 3 * kATile;
@@ -126,6 +160,7 @@ __global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S,
   uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int am = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
   if (tid == 0) umma::mbar_init(mbar, 1);
   if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
   sync_all();
@@ -134,41 +169,52 @@ __global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S,
   const size_t plane = (size_t)LD * LD;
   uint32_t phase = 0;
   bool ok = true;
-  const int row = warp * 32 + lane;  // TMEM lane = tile row = l - l0
+  const int row = quad * 32 + lane;  // TMEM lane = tile row = l - l0
   for (int gi = 0; gi < ng; ++gi) {
     const SpinGroup& g = groups[gi];
     const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
     const int lstart = max(max(l0, am), as);
-    float ahi[kN], alo[kN];
+    float ahi[16], alo[16];
 #pragma unroll
-    for (int j = 0; j < kN; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
+    for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
     if (lstart < l1) {
       for (int mp0 = 0; mp0 < l1; mp0 += kKTile) {
-        for (int idx = tid; idx < 128 * kKTile; idx += 128) {
-          const int r = idx / kKTile, k = idx % kKTile;
-          const int l = l0 + r, mp = mp0 + k;
-          float x = 0.f;
+        // A: 128 rows x 8 chunks of 8 m'
+        for (int task = tid; task < 128 * (kKTile / 8); task += kThreads) {
+          const int r = task >> 3, c = task & 7;
+          const int l = l0 + r, mp = mp0 + 8 * c;
+          float x[8];
           if (l >= lstart && l < l1 && mp <= l) {
-            const float* P = S + (size_t)(l - l0) * plane;
-            x = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
-            if ((am + as + (s > 0 ? l + mp : 0)) & 1) x = -x;
+            kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, x);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = 0.f;
           }
-          store_split(sA, kATile, umma::tile_off(r, k, kKTile / 8), x);
+          store_split8(sA, kATile, umma::tile_off(r, 8 * c, kKTile / 8), x);
         }
-        for (int idx = tid; idx < kN * kKTile; idx += 128) {
-          const int n = idx / kKTile, k = idx % kKTile;
-          const int j = n >> 1, mp = mp0 + k;
-          float x = 0.f;
-          if (j < 2 * nb && mp < L) {
+        // B: 32 rows (map, re/im; +am then -am) x 8 chunks
+        for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
+          const int n = task >> 3, c = task & 7;
+          const int j = n >> 1, mp = mp0 + 8 * c;
+          float x[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = 0.f;
+          if (j < 2 * nb) {
             const bool neg = j >= nb;
             if (!(neg && am == 0)) {
-              const int b = g.maps[neg ? j - nb : j];
-              const float2 v = Gp[((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp];
-              x = (n & 1) ? v.y : v.x;
-              if (neg && (mp & 1)) x = -x;
+              const float2* src = Gp + ((size_t)g.maps[neg ? j - nb : j] * M + (neg ? -am : am) + L - 1) * L;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                if (mp + i < L) {
+                  const float2 v = src[mp + i];
+                  float y = (n & 1) ? v.y : v.x;
+                  if (neg && ((mp + i) & 1)) y = -y;
+                  x[i] = y;
+                }
+              }
             }
           }
-          store_split(sB, kBTile, umma::tile_off(n, k, kKTile / 8), x);
+          store_split8(sB, kBTile, umma::tile_off(n, 8 * c, kKTile / 8), x);
         }
         umma::fence_proxy_async();
         sync_all();
@@ -179,29 +225,34 @@ __global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S,
         const bool w = wait_all(mbar, phase);
         phase ^= 1u;
         ok = ok && w;
-        if (w) drain_slots(tmem, warp, ahi, alo);
+        if (w) drain_half(tmem, quad, half, ahi, alo);
         sync_all();
       }
     }
-    // epilogue: times (-1)^s i^(m+s) N_l (and (-1)^l for m = -am)
+    // epilogue: columns 16*half .. +15 = (map j, re/im) for j = 8*half .. 8*half+7
     const int l = l0 + row;
-    if (l >= am && l >= l0 && l < l1) {
-      const double nl = ((s & 1) ? -1.0 : 1.0) * sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+    if (l >= am && l < l1) {
+      const double nl = ((s & 1) ? -1.0 : 1.0) * nltab[l];
 #pragma unroll
-      for (int j = 0; j < 2 * kTcGroupMaps; ++j) {
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = 8 * half + jj;
         if (j >= 2 * nb) continue;
         const bool neg = j >= nb;
         if (neg && am == 0) continue;
         const int m = neg ? -am : am;
         double2 o = make_double2(0.0, 0.0);
         if (l >= as) {
-          double ar = (double)ahi[2 * j] + (double)alo[2 * j], ai = (double)ahi[2 * j + 1] + (double)alo[2 * j + 1];
-          if (neg && (l & 1)) { ar = -ar; ai = -ai; }
-          const int r4 = (m + s) & 3;
-          const double pr = (r4 == 0) ? 1.0 : (r4 == 2 ? -1.0 : 0.0);
-          const double pi_ = (r4 == 1) ? 1.0 : (r4 == 3 ? -1.0 : 0.0);
-          o.x = nl * (pr * ar - pi_ * ai);
-          o.y = nl * (pr * ai + pi_ * ar);
+          double ar = (double)ahi[2 * jj] + (double)alo[2 * jj];
+          double ai = (double)ahi[2 * jj + 1] + (double)alo[2 * jj + 1];
+          const double sgn = (neg && (l & 1)) ? -nl : nl;
+          ar *= sgn;
+          ai *= sgn;
+          switch ((m + s) & 3) {  // times i^(m+s)
+            case 0: o = make_double2(ar, ai); break;
+            case 1: o = make_double2(-ai, ar); break;
+            case 2: o = make_double2(-ar, -ai); break;
+            default: o = make_double2(ai, -ar); break;
+          }
         }
         flm[(size_t)g.maps[neg ? j - nb : j] * L * L + (size_t)l * l + l + m] = o;
       }
@@ -214,12 +265,17 @@ __global__ void __launch_bounds__(128) k_tc_forward(const float* __restrict__ S,
 
 // ---------------------------------------------------------------------------
 // inverse: F+_{+-am, m'} += sum_{l in [l0,l1)} N_l Delta^l_{m',am} Delta^l_{m',-s} f_{l,+-am}
-// one block per (am, 128-row tile of m', spin group)
+// one block per (am, 128-row tile of m', spin group).  The A operand (rows m',
+// K = l) is stored MN-major: each 16-byte core-matrix row holds 8 consecutive m'
+// of one l, exactly the layout of a plane row.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
-                                                    int l1, const SpinGroup* __restrict__ groups,
-                                                    const double2* __restrict__ flm, double2* __restrict__ Fp,
-                                                    int* __restrict__ err) {
+constexpr int kMnSbo = 128;                  // stride between 8-m' groups
+constexpr int kMnLbo = (128 / 8) * 128;      // stride between 8-l groups (2048)
+
+__global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
+                                                         int l1, const SpinGroup* __restrict__ groups,
+                                                         const float2* __restrict__ flmf, double2* __restrict__ Fp,
+                                                         int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
   unsigned char* sB = smem + 3 * kATile;
@@ -230,79 +286,101 @@ __global__ void __launch_bounds__(128) k_tc_inverse(const float* __restrict__ S,
   const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
   const int lstart = max(max(l0, am), as);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
   if (lstart >= l1 || mp0 >= l1) return;  // block-uniform: nothing to add
   if (tid == 0) umma::mbar_init(mbar, 1);
   if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
   sync_all();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = umma::idesc_bf16_f32(128, kN);
+  const uint32_t idesc = umma::idesc_bf16_f32(128, kN) | (1u << 15);  // A MN-major
   const size_t plane = (size_t)LD * LD;
   uint32_t phase = 0;
   bool ok = true;
-  float ahi[kN], alo[kN];
+  float ahi[16], alo[16];
 #pragma unroll
-  for (int j = 0; j < kN; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
+  for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
   for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
     const int lb = l0 + kt * kKTile;
-    for (int idx = tid; idx < 128 * kKTile; idx += 128) {
-      const int r = idx % 128, k = idx / 128;
-      const int l = lb + k, mp = mp0 + r;
-      float x = 0.f;
-      if (l >= lstart && l < l1 && mp <= l) {
-        const float* P = S + (size_t)(l - l0) * plane;
-        x = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
-        if ((am + as + (s > 0 ? l + mp : 0)) & 1) x = -x;
+    // A: 64 l x 16 chunks of 8 m'
+    for (int task = tid; task < kKTile * 16; task += kThreads) {
+      const int k = task >> 4, c = task & 15;
+      const int l = lb + k, mp = mp0 + 8 * c;
+      float x[8];
+      if (l >= lstart && l < l1 && mp <= l && mp < L) {
+        kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, x);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = 0.f;
       }
-      store_split(sA, kATile, umma::tile_off(r, k, kKTile / 8), x);
+      store_split8(sA, kATile, c * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, x);
     }
-    for (int idx = tid; idx < kN * kKTile; idx += 128) {
-      const int n = idx / kKTile, k = idx % kKTile;
-      const int j = n >> 1, l = lb + k;
-      float x = 0.f;
-      if (j < 2 * nb && l >= lstart && l < l1) {
+    // B: 32 rows (map, re/im) x 8 chunks of 8 l (K-major)
+    for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
+      const int n = task >> 3, c = task & 7;
+      const int j = n >> 1;
+      float x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = 0.f;
+      if (j < 2 * nb) {
         const bool neg = j >= nb;
         if (!(neg && am == 0)) {
           const int b = g.maps[neg ? j - nb : j];
-          const double2 f = flm[(size_t)b * L * L + (size_t)l * l + l + (neg ? -am : am)];
-          const double nl = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
-          double v = ((n & 1) ? f.y : f.x) * nl;
-          if (neg && (l & 1)) v = -v;
-          x = (float)v;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int l = lb + 8 * c + i;
+            if (l >= lstart && l < l1) {
+              const float2 f = flmf[(size_t)b * L * L + (size_t)l * l + l + (neg ? -am : am)];  // N_l f_lm
+              float y = (n & 1) ? f.y : f.x;
+              if (neg && (l & 1)) y = -y;
+              x[i] = y;
+            }
+          }
         }
       }
-      store_split(sB, kBTile, umma::tile_off(n, k, kKTile / 8), x);
+      store_split8(sB, kBTile, umma::tile_off(n, 8 * c, kKTile / 8), x);
     }
     umma::fence_proxy_async();
     sync_all();
     if (tid == 0) {
-      issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+#pragma unroll
+      for (int ks = 0; ks < kKTile / 16; ++ks) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const uint64_t ad =
+              umma::smem_desc(umma::smem_u32(sA) + split_a(p) * kATile + ks * 2 * kMnLbo, kMnLbo, kMnSbo);
+          const uint64_t bd =
+              umma::smem_desc(umma::smem_u32(sB) + split_b(p) * kBTile + ks * 256, 128, (kKTile / 8) * 128);
+          const int slt = (p == 0) ? ks : (p < 3 ? 4 : 5);
+          const int acc = (p == 0) ? 0 : ((ks == 0 && (p == 1 || p == 3)) ? 0 : 1);
+          umma::mma_bf16(tmem + (uint32_t)(slt * kN), ad, bd, idesc, acc);
+        }
+      }
       umma::commit(mbar);
     }
     const bool w = wait_all(mbar, phase);
     phase ^= 1u;
     ok = ok && w;
     if (!ok) break;
-    drain_slots(tmem, warp, ahi, alo);
+    drain_half(tmem, quad, half, ahi, alo);
     sync_all();
   }
   // epilogue: add the chunk's sum into the FP64 accumulator F+
-  const int mp = mp0 + warp * 32 + lane;
-  if (ok) {
-    if (mp < L && mp < l1) {
+  const int mp = mp0 + quad * 32 + lane;
+  if (ok && mp < L && mp < l1) {
 #pragma unroll
-      for (int j = 0; j < 2 * kTcGroupMaps; ++j) {
-        if (j >= 2 * nb) continue;
-        const bool neg = j >= nb;
-        if (neg && am == 0) continue;
-        const int b = g.maps[neg ? j - nb : j];
-        double2* dst = Fp + ((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp;
-        double re = (double)ahi[2 * j] + (double)alo[2 * j], im = (double)ahi[2 * j + 1] + (double)alo[2 * j + 1];
-        if (neg && (mp & 1)) { re = -re; im = -im; }
-        double2 cur = *dst;
-        cur.x += re;
-        cur.y += im;
-        *dst = cur;
-      }
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = 8 * half + jj;
+      if (j >= 2 * nb) continue;
+      const bool neg = j >= nb;
+      if (neg && am == 0) continue;
+      const int b = g.maps[neg ? j - nb : j];
+      double2* dst = Fp + ((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp;
+      double re = (double)ahi[2 * jj] + (double)alo[2 * jj], im = (double)ahi[2 * jj + 1] + (double)alo[2 * jj + 1];
+      if (neg && (mp & 1)) { re = -re; im = -im; }
+      double2 cur = *dst;
+      cur.x += re;
+      cur.y += im;
+      *dst = cur;
     }
   }
   if (!ok && tid == 0) atomicExch(err, 1);
@@ -312,19 +390,35 @@ __global__ void __launch_bounds__(128) k_tc_inverse(const float* __restrict__ S,
 
 }  // namespace
 
-cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  if (e != cudaSuccess) return e;
-  k_tc_forward<<<l1, 128, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
-                                       reinterpret_cast<const float2*>(p->d_Gp), flm, p->d_err);
+// N_l f_lm in FP32 for the inverse contraction (one block per (l, map)).
+__global__ void k_flm_to_f32(const double2* __restrict__ flm, float2* __restrict__ out, int L) {
+  const int l = blockIdx.x, b = blockIdx.y;
+  const float nl = sqrtf((2.f * l + 1.f) / (4.f * 3.14159265358979f));
+  const size_t base = (size_t)b * L * L + (size_t)l * l;
+  for (int i = threadIdx.x; i < 2 * l + 1; i += blockDim.x) {
+    const double2 v = flm[base + i];
+    out[base + i] = make_float2((float)v.x * nl, (float)v.y * nl);
+  }
+}
+
+cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t st) {
+  k_flm_to_f32<<<dim3(p->L, p->B), 128, 0, st>>>(flm, p->d_flmf, p->L);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st) {
+cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  k_tc_forward<<<l1, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
+                                       reinterpret_cast<const float2*>(p->d_Gp), p->d_nl, flm, p->d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const float2* flm, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
   const dim3 grid(l1, (l1 + 127) / 128, (unsigned)p->groups.size());
-  k_tc_inverse<<<grid, 128, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, flm,
+  k_tc_inverse<<<grid, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, flm,
                                          reinterpret_cast<double2*>(p->d_Gp), p->d_err);
   return cudaGetLastError();
 }

@@ -30,43 +30,179 @@ namespace {
 
 __device__ __forceinline__ double sgn_pow(int k) { return (k & 1) ? -1.0 : 1.0; }
 
-// new plane 2j' = two_jp from old plane (j = j' - 1/2)
-__global__ void k_risbo_half(const double* __restrict__ d, double* __restrict__ e, int two_jp, int LD,
-                             const double* __restrict__ sq, double scale, float* __restrict__ stage) {
-  const int odd = two_jp & 1;                // j' half-integer
-  const int nnew = odd ? (two_jp + 1) / 2 : two_jp / 2 + 1;
-  const int nold = (two_jp + 1) / 2;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y * blockDim.y + threadIdx.y;
-  if (a >= nnew || b >= nnew) return;
-  const int mu2 = 2 * a + odd, nu2 = 2 * b + odd;  // twice mu, nu
-  const int jo2 = two_jp - 1;                      // twice the old j
-  const double cmm = sq[(two_jp - mu2) / 2], cpm = sq[(two_jp + mu2) / 2];
-  const double cmn = sq[(two_jp - nu2) / 2], cpn = sq[(two_jp + nu2) / 2];
-  // old indices of mu +- 1/2 and nu +- 1/2
-  const int ip = a + odd, im = a - 1 + odd;
-  const int jp = b + odd, jm = b - 1 + odd;
-  auto at = [&](int i, int k) -> double {
-    if (i >= nold || k >= nold) return 0.0;
-    double sgn = 1.0;
-    // only -1/2 can occur (integer new plane, old half-integer plane)
-    if (i < 0) {  // d_{-1/2, n} = (-1)^(j - n) d_{1/2, n},  n = k + 1/2
-      const int n2 = (k < 0) ? -1 : 2 * k + 1;
-      sgn *= sgn_pow((jo2 - n2) / 2);
-      i = 0;
+// v * (-1)^k by flipping the sign bit on the integer pipe (the FP64 pipe is the
+// bottleneck of the recursion on this part)
+__device__ __forceinline__ double flip_sign(double v, int k) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(k & 1) << 63));
+}
+
+// double -> float, round to nearest (ties away), on the integer pipe; values
+// below 2^-126 in magnitude (irrelevant for |Delta| <= 1 at the 1e-6 level)
+// become signed zero.  |v| <= 1 here, so there is no overflow.
+__device__ __forceinline__ float to_f32_int(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e <= 896) return __uint_as_float(sign);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const unsigned f = ((unsigned)(e - 896) << 23) + (unsigned)((m + (1ull << 28)) >> 29);
+  return __uint_as_float(sign | f);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent Risbo sweep over the planes l in [l_begin, l_end) of one chunk.
+//
+// One cooperative launch per chunk; a grid-wide barrier (bounded spin) separates
+// the half steps.  Each half step computes only the lower triangle b <= a of the
+// new quarter plane in 32 x 32 tiles (the transpose symmetry supplies the rest),
+// staging the old plane's tile plus a one-element halo in shared memory.  Per
+// element the stencil costs 6 FP64 instructions: with pre-scaled column factors
+// cn = sqrt(j'-nu)/(2 sqrt2 j') and cp = sqrt(j'+nu)/(2 sqrt2 j'),
+//   e = cn (sqrt(j'-mu) d_{+,+} - sqrt(j'+mu) d_{-,+}) + cp (sqrt(j'-mu) d_{+,-} + sqrt(j'+mu) d_{-,-}).
+// Integer planes are also written out as full quarters where a contraction
+// reads them (FP32 staging copy on the mixed path; the FP64 plane itself on the
+// FP64 path), the upper triangle through an in-shared-memory transpose.
+// ---------------------------------------------------------------------------
+constexpr int kRT = 32;         // tile edge
+constexpr int kRThreads = 256;  // 32 x 8 threads, 4 rows each
+constexpr unsigned kBarrierPolls = 1u << 24;
+
+struct RisboArgs {
+  double* S;          // FP64 integer planes; plane l at slot l % nslot
+  int nslot;
+  double* H;          // half-integer plane
+  float* S32;         // FP32 staging of the integer planes (slot l - l0), or null
+  int l0;
+  int full64;         // write transposed tiles into the FP64 integer plane
+  int LD;
+  const double* sq;   // sqrt(k)
+  const double* rscale;  // 1 / (sqrt2 two_jp)
+  unsigned* bar;      // grid barrier counter (zeroed before the launch)
+  int* err;
+};
+
+// Old-plane value d[i][k] (indices of the quarter storage, possibly -1 or above
+// the diagonal), through the pi/2 symmetries; zero beyond the plane.
+__device__ __forceinline__ double old_val(const double* __restrict__ d, int LD, int i, int k, int nold, int jo2) {
+  if (i >= nold || k >= nold) return 0.0;
+  int ex = 0;  // the value is (-1)^ex d[i][k]
+  if (i < 0) {  // d_{-1/2, n} = (-1)^(j - n) d_{1/2, n}
+    const int n2 = (k < 0) ? -1 : 2 * k + 1;
+    ex += (jo2 - n2) / 2;
+    i = 0;
+  }
+  if (k < 0) {  // d_{m, -1/2} = (-1)^(j + m) d_{m, 1/2}
+    ex += (jo2 + 2 * i + 1) / 2;
+    k = 0;
+  }
+  if (k > i) {  // d_{mn} = (-1)^(m-n) d_{nm}
+    ex += i - k;
+    const int t = i; i = k; k = t;
+  }
+  return flip_sign(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks in the last half step
+}
+
+// Grid-wide barrier for a cooperative launch; gives up after kBarrierPolls polls,
+// records the timeout in *err and returns false (every block then leaves).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned& gen, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen += 1;
+    const unsigned target = gen * gridDim.x;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    unsigned polls = 0;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if (++polls > kBarrierPolls) { ok = 0; atomicOr(err, 2); break; }
+      __nanosleep(20);
     }
-    if (k < 0) {  // d_{m, -1/2} = (-1)^(j + m) d_{m, 1/2},  m = i + 1/2 (after the row reflection)
-      const int m2 = 2 * i + 1;
-      sgn *= sgn_pow((jo2 + m2) / 2);
-      k = 0;
+    __threadfence();
+    if (ok && *(volatile int*)err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
+  __shared__ double halo[kRT + 2][kRT + 3];
+  __shared__ double tr[kRT][kRT + 1];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int LD = A.LD;
+  const size_t plane = (size_t)LD * LD;
+  unsigned gen = 0;
+  for (int l = l_begin; l < l_end; ++l) {
+    for (int h = 0; h < 2; ++h) {
+      const int two_jp = 2 * l - 1 + h;
+      const int odd = two_jp & 1;
+      const int nnew = odd ? (two_jp + 1) / 2 : two_jp / 2 + 1;
+      const int nold = (two_jp + 1) / 2;
+      const int jo2 = two_jp - 1;
+      const double* d = (h == 0) ? A.S + (size_t)((l - 1) % A.nslot) * plane : A.H;
+      double* e = (h == 0) ? A.H : A.S + (size_t)(l % A.nslot) * plane;
+      float* st = (h == 1 && A.S32) ? A.S32 + (size_t)(l - A.l0) * plane : nullptr;
+      const bool full64 = (h == 1) && A.full64;
+      const double sc = A.rscale[two_jp];  // table: an FP64 division per thread is expensive here
+      const int T = (nnew + kRT - 1) / kRT;
+      const int ntiles = T * (T + 1) / 2;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+        while (I * (I + 1) / 2 > t) --I;
+        while ((I + 1) * (I + 2) / 2 <= t) ++I;
+        const int J = t - I * (I + 1) / 2;
+        const int a0 = I * kRT, b0 = J * kRT;
+        for (int idx = tid; idx < (kRT + 2) * (kRT + 2); idx += kRThreads) {
+          const int r = idx / (kRT + 2), c = idx % (kRT + 2);
+          halo[r][c] = old_val(d, LD, a0 - 1 + r, b0 - 1 + c, nold, jo2);
+        }
+        __syncthreads();
+        const int b = b0 + tx;
+        const int nu2 = 2 * b + odd;
+        const bool bok = b < nnew;
+        const double cn = bok ? sc * A.sq[(two_jp - nu2) / 2] : 0.0;
+        const double cp = bok ? sc * A.sq[(two_jp + nu2) / 2] : 0.0;
+        const bool need_tr = (J < I) && (st || full64);
+#pragma unroll
+        for (int q = 0; q < kRT / 8; ++q) {
+          const int r = ty + 8 * q;
+          const int a = a0 + r;
+          double v = 0.0;
+          if (a < nnew && bok) {
+            const int mu2 = 2 * a + odd;
+            const double cmm = A.sq[(two_jp - mu2) / 2], cpm = A.sq[(two_jp + mu2) / 2];
+            const double dpp = halo[r + 1 + odd][tx + 1 + odd], dmp = halo[r + odd][tx + 1 + odd];
+            const double dpm = halo[r + 1 + odd][tx + odd], dmm = halo[r + odd][tx + odd];
+            const double t1 = fma(-cpm, dmp, cmm * dpp);
+            const double t2 = fma(cpm, dmm, cmm * dpm);
+            v = fma(cp, t2, cn * t1);
+            e[(size_t)a * LD + b] = v;
+            if (st) st[(size_t)a * LD + b] = to_f32_int(v);
+          }
+          if (need_tr) tr[r][tx] = v;
+        }
+        if (need_tr) {
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < kRT / 8; ++q) {
+            const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
+            if (aa < nnew && bb < nnew) {
+              const double v = flip_sign(tr[tx][ty + 8 * q], aa - bb);
+              if (full64) e[(size_t)bb * LD + aa] = v;
+              if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      const bool last = (l == l_end - 1) && (h == 1);
+      if (!last && !grid_sync(A.bar, gen, A.err)) return;
     }
-    return sgn * d[(size_t)i * LD + k];
-  };
-  const double dpp = at(ip, jp), dmp = at(im, jp), dpm = at(ip, jm), dmm = at(im, jm);
-  const double v = cmn * (cmm * dpp - cpm * dmp) + cpn * (cmm * dpm + cpm * dmm);
-  const double out = scale * v;
-  e[(size_t)a * LD + b] = out;
-  if (stage) stage[(size_t)a * LD + b] = (float)out;  // FP32 copy for the tensor-core contraction
+  }
 }
 
 __global__ void k_plane_init(double* S, float* S32) {
@@ -82,7 +218,7 @@ constexpr int kTileMp = 64;
 
 __global__ void k_contract_forward(const double* __restrict__ S, int LD, int L, int M, int l0, int l1,
                                    const SpinGroup* __restrict__ groups, const double2* __restrict__ Gp,
-                                   double2* __restrict__ flm) {
+                                   double2* __restrict__ flm, const double* __restrict__ nltab) {
   __shared__ double Kt[kChunk][kTileMp + 1];
   __shared__ double2 Gs[kMaxGroupMaps][kTileMp];
   const int im = blockIdx.x, m = im - (L - 1), am = m < 0 ? -m : m;
@@ -152,7 +288,7 @@ __global__ void k_contract_forward(const double* __restrict__ S, int LD, int L, 
       if (l < lstart) continue;
       double2 o = make_double2(0.0, 0.0);
       if (l >= as) {
-        const double nl_ = sgs * sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+        const double nl_ = sgs * nltab[l];
         o.x = nl_ * (pr * ar[q] - pi_ * ai[q]);
         o.y = nl_ * (pr * ai[q] + pi_ * ar[q]);
       }
@@ -167,7 +303,7 @@ __global__ void k_contract_forward(const double* __restrict__ S, int LD, int L, 
 // One block per (m, m'-tile, spin group).
 __global__ void k_contract_inverse(const double* __restrict__ S, int LD, int L, int M, int l0, int l1,
                                    const SpinGroup* __restrict__ groups, const double2* __restrict__ flm,
-                                   double2* __restrict__ Fp) {
+                                   double2* __restrict__ Fp, const double* __restrict__ nltab) {
   __shared__ double Kt[kChunk][kTileMp + 1];
   __shared__ double2 Fs[kMaxGroupMaps][kChunk];
   const int im = blockIdx.x, m = im - (L - 1), am = m < 0 ? -m : m;
@@ -187,7 +323,7 @@ __global__ void k_contract_inverse(const double* __restrict__ S, int LD, int L, 
       int ex = am + as;
       if (m < 0) ex += l + mp;
       if (s > 0) ex += l + mp;
-      k = sgn_pow(ex) * v * sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+      k = sgn_pow(ex) * v * nltab[l];
     }
     Kt[r][c] = k;
   }
@@ -217,6 +353,20 @@ __global__ void k_contract_inverse(const double* __restrict__ S, int LD, int L, 
 
 namespace {
 
+cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, int full64, int lb, int le,
+                         cudaStream_t st, int* nd) {
+  if (lb >= le) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(p->d_bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  RisboArgs a;
+  a.S = S; a.nslot = nslot; a.H = p->d_H; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
+  a.sq = p->d_sqrt; a.rscale = p->d_rscale; a.bar = p->d_bar; a.err = p->d_err;
+  void* args[] = {&a, &lb, &le};
+  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args, 0, st);
+  if (nd) *nd += 1;
+  return e;
+}
+
 cudaError_t run_wigner_fp64(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
                             int* launches) {
   const int L = p->L, M = p->M, LD = p->LD;
@@ -233,29 +383,17 @@ cudaError_t run_wigner_fp64(mw_plan* p, int mode, const double2* flm_in, double2
     const int l1 = (l0 + kChunk < L) ? l0 + kChunk : L;
     StageSpan span_d(p, MW_STAGE_DELTA, st);
     int nd = 0;
-    for (int l = (l0 == 0 ? 1 : l0); l < l1; ++l) {
-      const double* prev = p->d_S + (size_t)((l - 1) % kChunk) * LD * LD;
-      double* cur = p->d_S + (size_t)(l % kChunk) * LD * LD;
-      // half-integer plane j' = l - 1/2, then integer plane j' = l
-      for (int h = 0; h < 2; ++h) {
-        const int two_jp = 2 * l - 1 + h;
-        const int nnew = (two_jp & 1) ? (two_jp + 1) / 2 : two_jp / 2 + 1;
-        const dim3 blk(32, 8);
-        const dim3 grd((nnew + 31) / 32, (nnew + 7) / 8);
-        const double scale = 1.0 / (sqrt(2.0) * (double)two_jp);
-        k_risbo_half<<<grd, blk, 0, st>>>(h == 0 ? prev : p->d_H, h == 0 ? p->d_H : cur, two_jp, LD, p->d_sqrt,
-                                          scale, nullptr);
-        ++nd;
-      }
-    }
+    e = launch_risbo(p, p->d_S, kChunk, nullptr, l0, 1, (l0 == 0 ? 1 : l0), l1, st, &nd);
+    if (e != cudaSuccess) return e;
     span_d.end(nd);
     nl += nd;
     StageSpan span_c(p, MW_STAGE_CONTRACT, st);
     if (mode == 0) {
-      k_contract_forward<<<dim3(M, ng), 256, 0, st>>>(p->d_S, LD, L, M, l0, l1, p->d_groups, p->d_Gp, flm_out);
+      k_contract_forward<<<dim3(M, ng), 256, 0, st>>>(p->d_S, LD, L, M, l0, l1, p->d_groups, p->d_Gp, flm_out,
+                                                      p->d_nl);
     } else {
-      k_contract_inverse<<<dim3(M, (l1 + kTileMp - 1) / kTileMp, ng), 256, 0, st>>>(p->d_S, LD, L, M, l0, l1,
-                                                                                     p->d_groups, flm_in, p->d_Gp);
+      k_contract_inverse<<<dim3(M, (l1 + kTileMp - 1) / kTileMp, ng), 256, 0, st>>>(
+          p->d_S, LD, L, M, l0, l1, p->d_groups, flm_in, p->d_Gp, p->d_nl);
     }
     span_c.end(1);
     ++nl;
@@ -270,13 +408,15 @@ cudaError_t run_wigner_fp64(mw_plan* p, int mode, const double2* flm_in, double2
 // integer planes of a 128-plane chunk for the tensor-core contraction.
 cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
                              int* launches) {
-  const int L = p->L, M = p->M, LD = p->LD;
-  const size_t plane = (size_t)LD * LD;
+  const int L = p->L, M = p->M;
   int nl = 0;
   cudaError_t e;
   if (mode == 1) {
     e = cudaMemsetAsync(p->d_Gp, 0, sizeof(double2) * (size_t)p->B * M * L, st);
     if (e != cudaSuccess) return e;
+    e = launch_flm_to_f32(p, flm_in, st);
+    if (e != cudaSuccess) return e;
+    ++nl;
   }
   k_plane_init<<<1, 1, 0, st>>>(p->d_S, p->d_S32);
   ++nl;
@@ -284,24 +424,12 @@ cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double
     const int l1 = (l0 + kTcChunk < L) ? l0 + kTcChunk : L;
     StageSpan span_d(p, MW_STAGE_DELTA, st);
     int nd = 0;
-    for (int l = (l0 == 0 ? 1 : l0); l < l1; ++l) {
-      const double* prev = p->d_S + (size_t)((l - 1) & 1) * plane;
-      double* cur = p->d_S + (size_t)(l & 1) * plane;
-      for (int h = 0; h < 2; ++h) {
-        const int two_jp = 2 * l - 1 + h;
-        const int nnew = (two_jp & 1) ? (two_jp + 1) / 2 : two_jp / 2 + 1;
-        const dim3 blk(32, 8);
-        const dim3 grd((nnew + 31) / 32, (nnew + 7) / 8);
-        const double scale = 1.0 / (sqrt(2.0) * (double)two_jp);
-        k_risbo_half<<<grd, blk, 0, st>>>(h == 0 ? prev : p->d_H, h == 0 ? p->d_H : cur, two_jp, LD, p->d_sqrt,
-                                          scale, h == 0 ? nullptr : p->d_S32 + (size_t)(l - l0) * plane);
-        ++nd;
-      }
-    }
+    e = launch_risbo(p, p->d_S, 2, p->d_S32, l0, 0, (l0 == 0 ? 1 : l0), l1, st, &nd);
+    if (e != cudaSuccess) return e;
     span_d.end(nd);
     nl += nd;
     StageSpan span_c(p, MW_STAGE_CONTRACT, st);
-    e = (mode == 0) ? launch_tc_forward(p, l0, l1, flm_out, st) : launch_tc_inverse(p, l0, l1, flm_in, st);
+    e = (mode == 0) ? launch_tc_forward(p, l0, l1, flm_out, st) : launch_tc_inverse(p, l0, l1, p->d_flmf, st);
     span_c.end(1);
     ++nl;
     if (e != cudaSuccess) return e;
@@ -311,6 +439,15 @@ cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double
 }
 
 }  // namespace
+
+int risbo_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n < 1 ? 1 : (n > 4 ? 4 : n);
+}
 
 cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
                        int* launches) {

@@ -65,7 +65,7 @@ cudaError_t upload_complex(const std::vector<double>& re, const std::vector<doub
 void free_plan(mw_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
-                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err};
+                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err, p->d_bar, p->d_rscale, p->d_nl, p->d_flmf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -98,7 +98,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   p->N = N;
   p->flags = flags;
   p->prec = prec;
-  p->LD = L + 1;
+  p->LD = ((L + 1 + 7) / 8) * 8;  // 32-byte aligned plane rows
   cudaGetDevice(&p->device);
   p->spins.assign(spins, spins + B);
   if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
@@ -195,6 +195,15 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     alloc((void**)&p->d_upole, sizeof(double) * up.size());
     if (e == cudaSuccess) chk(cudaMemcpy(p->d_upole, up.data(), sizeof(double) * up.size(), cudaMemcpyHostToDevice));
   }
+  {
+    std::vector<double> rs(2 * L + 2, 0.0), nlv(L);
+    for (int k = 1; k < (int)rs.size(); ++k) rs[k] = 1.0 / (std::sqrt(2.0) * (double)k);
+    for (int l = 0; l < L; ++l) nlv[l] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+    alloc((void**)&p->d_rscale, sizeof(double) * rs.size());
+    if (e == cudaSuccess) chk(cudaMemcpy(p->d_rscale, rs.data(), sizeof(double) * rs.size(), cudaMemcpyHostToDevice));
+    alloc((void**)&p->d_nl, sizeof(double) * nlv.size());
+    if (e == cudaSuccess) chk(cudaMemcpy(p->d_nl, nlv.data(), sizeof(double) * nlv.size(), cudaMemcpyHostToDevice));
+  }
   alloc((void**)&p->d_spins, sizeof(int) * B);
   if (e == cudaSuccess) chk(cudaMemcpy(p->d_spins, spins, sizeof(int) * B, cudaMemcpyHostToDevice));
   alloc((void**)&p->d_groups, sizeof(SpinGroup) * p->groups.size());
@@ -209,8 +218,15 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   alloc((void**)&p->d_S, sizeof(double) * (dbl ? (size_t)kChunk : 2) * plane);
   alloc((void**)&p->d_H, sizeof(double) * plane);
   if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)kTcChunk * plane);
+  if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
   alloc((void**)&p->d_err, sizeof(int));
   if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
+  alloc((void**)&p->d_bar, sizeof(unsigned));
+  if (e == cudaSuccess) {
+    int nsm = 0;
+    chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    p->risbo_grid = nsm * risbo_blocks_per_sm();
+  }
   if (e != cudaSuccess) {
     const mw_status st = from_cuda(e);
     cudaGetLastError();
