@@ -1,13 +1,16 @@
 // fft.cuh -- in-place mixed-radix FFT of one sequence held in shared memory.
 //
-// Stockham formulation: stage k with radix R and span Ns = R_0...R_{k-1} writes
-//   out[o] = sum_{r<R} in[j + r n/R] * W_{Ns R}^{r (o mod Ns R)},
-//   j = (o / (Ns R)) Ns + (o mod Ns),   W_q = e^{-2 pi i / q},
-// which leaves the DFT in natural order after the last stage.  Every output is
-// an independent R-term dot product, so a thread computes its outputs into
-// registers, the block synchronises, and the outputs overwrite the inputs (one
-// shared buffer of n elements).  Odd prime radices (the 2L-1 lengths have
-// factors such as 73 or 127) use the same dot product; no Bluestein step is
+// Stockham autosort: stage k with radix R and span Ns = R_0...R_{k-1} takes, for
+// every butterfly j < n/R, the inputs x[j + r n/R] (r < R), multiplies input r
+// by W_{Ns R}^{r (j mod Ns)} (W_q = e^{-2 pi i / q}), applies an R-point DFT and
+// writes output k to position (j / Ns) Ns R + (j mod Ns) + k Ns; the result is in
+// natural order after the last stage.
+//
+// Radices 2, 3, 4, 5, 7 and 8 run as register butterflies: each thread loads
+// the inputs of its butterflies, the block synchronises, and the outputs
+// overwrite the inputs, so one shared buffer of n elements suffices.  Other odd
+// primes (the 2L-1 lengths contain factors such as 13, 31, 73 or 127) use a
+// dot-product stage in which each output is an R-term sum; no Bluestein step is
 // needed.  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
 #pragma once
 #include <cuda_runtime.h>
@@ -22,47 +25,268 @@ __device__ __forceinline__ typename cplx<T>::t mkc(T a, T b) {
   typename cplx<T>::t r; r.x = a; r.y = b; return r;
 }
 
-// forward: e^{-}, unnormalised; inverse (inv = true): e^{+}, unnormalised.
-// Requires blockDim.x * VPT >= d.n; all threads of the block must call it.
-template <typename T, int VPT>
-__device__ void fft_inplace(typename cplx<T>::t* buf, const FftDesc& d,
-                            const typename cplx<T>::t* __restrict__ tw, bool inv) {
-  typedef typename cplx<T>::t C;
-  const int n = d.n;
-  int Ns = 1;
-  for (int s = 0; s < d.nrad; ++s) {
-    const int R = d.rad[s], NsR = Ns * R, stride = n / R, step = n / NsR;
-    C val[VPT];
+namespace fftk {
+
+template <typename T> using C = typename cplx<T>::t;
+
+template <typename T> __device__ __forceinline__ C<T> add(C<T> a, C<T> b) { return mkc<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C<T> sub(C<T> a, C<T> b) { return mkc<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C<T> mul(C<T> a, C<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ C<T> mulc(C<T> a, C<T> b) {  // a * conj(b)
+  return mkc<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// times -i (forward) or +i (inverse)
+template <typename T> __device__ __forceinline__ C<T> rot(C<T> a, bool inv) {
+  return inv ? mkc<T>(-a.y, a.x) : mkc<T>(a.y, -a.x);
+}
+
+// cos and sin of 2 pi k / R for the odd radices (k = 1 .. (R-1)/2)
+__device__ __forceinline__ double cs3(int) { return -0.5; }
+__device__ __forceinline__ double sn3(int) { return 0.86602540378443864676; }
+__device__ __forceinline__ double cs5(int k) { return k == 1 ? 0.3090169943749474241 : -0.8090169943749474241; }
+__device__ __forceinline__ double sn5(int k) { return k == 1 ? 0.95105651629515357212 : 0.58778525229247312917; }
+__device__ __forceinline__ double cs7(int k) {
+  return k == 1 ? 0.62348980185873353053 : (k == 2 ? -0.22252093395631440429 : -0.90096886790241912624);
+}
+__device__ __forceinline__ double sn7(int k) {
+  return k == 1 ? 0.78183148246802980871 : (k == 2 ? 0.97492791218182360702 : 0.43388373911755812048);
+}
+
+// Odd R-point DFT by the symmetric pairing y_k = a_k +- i b_k with
+// a_k = v_0 + sum_r (v_r + v_{R-r}) cos(2 pi r k/R), b_k = sum_r (v_r - v_{R-r}) sin(2 pi r k/R).
+template <typename T, int R>
+__device__ __forceinline__ void dft_odd(C<T>* v, bool inv) {
+  constexpr int H = (R - 1) / 2;
+  C<T> s[H], d[H];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const int o = threadIdx.x + v * blockDim.x;
-      if (o < n) {
-        const int om = o % NsR;
-        const int j = (o / NsR) * Ns + (o % Ns);
-        T ar = 0, ai = 0;
-        int e = 0;
-        for (int r = 0; r < R; ++r) {
-          const C x = buf[j + r * stride];
-          const C w = tw[e * step];
-          const T wi = inv ? -w.y : w.y;
-          ar += x.x * w.x - x.y * wi;
-          ai += x.x * wi + x.y * w.x;
-          e += om;
-          if (e >= NsR) e -= NsR;
-        }
-        val[v] = mkc<T>(ar, ai);
-      }
-    }
-    __syncthreads();
+  for (int r = 1; r <= H; ++r) { s[r - 1] = add<T>(v[r], v[R - r]); d[r - 1] = sub<T>(v[r], v[R - r]); }
+  C<T> y0 = v[0];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const int o = threadIdx.x + v * blockDim.x;
-      if (o < n) buf[o] = val[v];
+  for (int r = 0; r < H; ++r) y0 = add<T>(y0, s[r]);
+  C<T> out[R];
+  out[0] = y0;
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    C<T> a = v[0], b = mkc<T>(0, 0);
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const int rk = (r * k) % R;
+      const int q = rk <= H ? rk : R - rk;         // cos(2pi rk/R) = cos(2pi q/R)
+      const T sg = rk <= H ? (T)1 : (T)-1;          // sin flips for rk > R/2
+      const T c = (T)(R == 3 ? cs3(q) : (R == 5 ? cs5(q) : cs7(q)));
+      const T sn = sg * (T)(R == 3 ? sn3(q) : (R == 5 ? sn5(q) : sn7(q)));
+      a.x += s[r - 1].x * c; a.y += s[r - 1].y * c;
+      b.x += d[r - 1].x * sn; b.y += d[r - 1].y * sn;
     }
-    __syncthreads();
-    Ns = NsR;
+    // forward: y_k = a - i b, y_{R-k} = a + i b (W = e^{-2 pi i/R}); inverse: swapped
+    const C<T> ib = mkc<T>(-b.y, b.x);
+    out[k] = inv ? add<T>(a, ib) : sub<T>(a, ib);
+    out[R - k] = inv ? sub<T>(a, ib) : add<T>(a, ib);
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(C<T>* v, bool inv) {
+  if constexpr (R == 2) {
+    const C<T> a = v[0], b = v[1];
+    v[0] = add<T>(a, b);
+    v[1] = sub<T>(a, b);
+  } else if constexpr (R == 4) {
+    const C<T> t0 = add<T>(v[0], v[2]), t1 = sub<T>(v[0], v[2]);
+    const C<T> t2 = add<T>(v[1], v[3]), t3 = rot<T>(sub<T>(v[1], v[3]), inv);
+    v[0] = add<T>(t0, t2);
+    v[2] = sub<T>(t0, t2);
+    v[1] = add<T>(t1, t3);
+    v[3] = sub<T>(t1, t3);
+  } else if constexpr (R == 8) {
+    const T h = (T)0.707106781186547524401;
+    C<T> a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { a[k] = add<T>(v[k], v[k + 4]); b[k] = sub<T>(v[k], v[k + 4]); }
+    // b_r *= W_8^r
+    b[1] = inv ? mkc<T>(h * (b[1].x - b[1].y), h * (b[1].x + b[1].y)) : mkc<T>(h * (b[1].x + b[1].y), h * (b[1].y - b[1].x));
+    b[2] = rot<T>(b[2], inv);
+    b[3] = inv ? mkc<T>(-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y)) : mkc<T>(h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y));
+    dft_small<T, 4>(a, inv);
+    dft_small<T, 4>(b, inv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { v[2 * k] = a[k]; v[2 * k + 1] = b[k]; }
+  } else {
+    dft_odd<T, R>(v, inv);
   }
 }
 
-constexpr int kFftVPT = 16;     // outputs per thread per stage
+// One register-butterfly stage of radix R.
+template <typename T, int R, int VPT>
+__device__ __forceinline__ void stage_reg(C<T>* buf, int n, int Ns, const C<T>* __restrict__ tw, bool inv) {
+  constexpr int BT = (VPT + R - 1) / R;
+  const int nb = n / R, step = n / (Ns * R);
+  C<T> v[BT][R];
+#pragma unroll
+  for (int q = 0; q < BT; ++q) {
+    const int j = threadIdx.x + q * blockDim.x;
+    if (j < nb) {
+      const int jm = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = buf[j + r * nb];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C<T> w = tw[(r * jm) * step];
+          v[q][r] = inv ? mulc<T>(v[q][r], w) : mul<T>(v[q][r], w);
+        }
+      }
+      dft_small<T, R>(v[q], inv);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < BT; ++q) {
+    const int j = threadIdx.x + q * blockDim.x;
+    if (j < nb) {
+      const int jm = j % Ns;
+      const int base = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Generic radix stage: every output an R-term dot product (odd primes > 7).
+template <typename T, int VPT>
+__device__ __forceinline__ void stage_dot(C<T>* buf, int n, int Ns, int R, const C<T>* __restrict__ tw, bool inv) {
+  const int NsR = Ns * R, stride = n / R, step = n / NsR;
+  C<T> val[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int o = threadIdx.x + v * blockDim.x;
+    if (o < n) {
+      const int om = o % NsR;
+      const int j = (o / NsR) * Ns + (o % Ns);
+      T ar = 0, ai = 0;
+      int e = 0;
+      for (int r = 0; r < R; ++r) {
+        const C<T> x = buf[j + r * stride];
+        const C<T> w = tw[e * step];
+        const T wi = inv ? -w.y : w.y;
+        ar += x.x * w.x - x.y * wi;
+        ai += x.x * wi + x.y * w.x;
+        e += om;
+        if (e >= NsR) e -= NsR;
+      }
+      val[v] = mkc<T>(ar, ai);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int o = threadIdx.x + v * blockDim.x;
+    if (o < n) buf[o] = val[v];
+  }
+  __syncthreads();
+}
+
+}  // namespace fftk
+
+// forward: e^{-}, unnormalised; inverse (inv = true): e^{+}, unnormalised.
+// Requires blockDim.x * VPT >= d.n; all threads of the block must call it.
+template <typename T, int VPT>
+__device__ void fft_inplace(typename cplx<T>::t* buf, const FftDesc& d, const typename cplx<T>::t* __restrict__ tw,
+                            bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < d.nrad; ++s) {
+    const int R = d.rad[s];
+    switch (R) {
+      case 2: fftk::stage_reg<T, 2, VPT>(buf, d.n, Ns, tw, inv); break;
+      case 3: fftk::stage_reg<T, 3, VPT>(buf, d.n, Ns, tw, inv); break;
+      case 4: fftk::stage_reg<T, 4, VPT>(buf, d.n, Ns, tw, inv); break;
+      case 5: fftk::stage_reg<T, 5, VPT>(buf, d.n, Ns, tw, inv); break;
+      case 7: fftk::stage_reg<T, 7, VPT>(buf, d.n, Ns, tw, inv); break;
+      case 8: fftk::stage_reg<T, 8, VPT>(buf, d.n, Ns, tw, inv); break;
+      default: fftk::stage_dot<T, VPT>(buf, d.n, Ns, R, tw, inv); break;
+    }
+    Ns *= R;
+  }
+}
+
+// Out-of-place variant: stages alternate between x and y (each n elements);
+// a thread holds one butterfly at a time.  Returns the buffer holding the result.
+namespace fftk {
+template <typename T, int R>
+__device__ __forceinline__ void stage_pp(const C<T>* __restrict__ in, C<T>* __restrict__ out, int n, int Ns,
+                                         const C<T>* __restrict__ tw, bool inv) {
+  const int nb = n / R, step = n / (Ns * R);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    C<T> v[R];
+    const int jm = j % Ns;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C<T> w = tw[(r * jm) * step];
+        v[r] = inv ? mulc<T>(v[r], w) : mul<T>(v[r], w);
+      }
+    }
+    dft_small<T, R>(v, inv);
+    const int base = (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_dot_pp(const C<T>* __restrict__ in, C<T>* __restrict__ out, int n, int Ns,
+                                             int R, const C<T>* __restrict__ tw, bool inv) {
+  const int NsR = Ns * R, stride = n / R, step = n / NsR;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    const int om = o % NsR;
+    const int j = (o / NsR) * Ns + (o % Ns);
+    T ar = 0, ai = 0;
+    int e = 0;
+    for (int r = 0; r < R; ++r) {
+      const C<T> x = in[j + r * stride];
+      const C<T> w = tw[e * step];
+      const T wi = inv ? -w.y : w.y;
+      ar += x.x * w.x - x.y * wi;
+      ai += x.x * wi + x.y * w.x;
+      e += om;
+      if (e >= NsR) e -= NsR;
+    }
+    out[o] = mkc<T>(ar, ai);
+  }
+  __syncthreads();
+}
+}  // namespace fftk
+
+template <typename T>
+__device__ typename cplx<T>::t* fft_pp(typename cplx<T>::t* x, typename cplx<T>::t* y, const FftDesc& d,
+                                       const typename cplx<T>::t* __restrict__ tw, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < d.nrad; ++s) {
+    const int R = d.rad[s];
+    switch (R) {
+      case 2: fftk::stage_pp<T, 2>(x, y, d.n, Ns, tw, inv); break;
+      case 3: fftk::stage_pp<T, 3>(x, y, d.n, Ns, tw, inv); break;
+      case 4: fftk::stage_pp<T, 4>(x, y, d.n, Ns, tw, inv); break;
+      case 5: fftk::stage_pp<T, 5>(x, y, d.n, Ns, tw, inv); break;
+      case 7: fftk::stage_pp<T, 7>(x, y, d.n, Ns, tw, inv); break;
+      case 8: fftk::stage_pp<T, 8>(x, y, d.n, Ns, tw, inv); break;
+      default: fftk::stage_dot_pp<T>(x, y, d.n, Ns, R, tw, inv); break;
+    }
+    typename cplx<T>::t* t = x;
+    x = y;
+    y = t;
+    Ns *= R;
+  }
+  return x;
+}
+
+constexpr int kFftVPT = 16;          // outputs per thread per stage (in-place variant)
 constexpr int kFftMaxThreads = 512;  // kFftVPT * kFftMaxThreads >= largest FFT (8192)

@@ -96,16 +96,16 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc 
   }
   for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = from64<T>(f[(long long)t * M + p]);
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, false);
   const T sc = (T)(2.0 * M_PI / M);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     const int m = i - (L - 1);
     const int k = m < 0 ? m + M : m;
-    out[(long long)i * L + t] = cscale<T>(buf[k], sc);
+    out[(long long)i * L + t] = cscale<T>(res[k], sc);
   }
 }
 
-template <typename T>
+template <typename T, bool PP>
 __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
                                 const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
                                 const C<T>* __restrict__ V, const C<T>* __restrict__ Gt, C<T>* __restrict__ Gp,
@@ -122,35 +122,51 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDes
   for (int t = threadIdx.x; t < M; t += blockDim.x)
     buf[t] = (t < L) ? g[t] : cscale<T>(g[2 * L - 2 - t], sg);
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
-  // F_mm' (times M 2pi, folded into V) with the half-sample phase, zero-padded to N
-  C<T> v[kFftVPT];
-#pragma unroll
-  for (int r = 0; r < kFftVPT; ++r) {
-    const int k = threadIdx.x + r * blockDim.x;
-    if (k < N) {
-      int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
-      if (mp == 0x7fffffff) v[r] = mkc<T>(0, 0);
-      else v[r] = cmul<T>(buf[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
+  C<T>* res;
+  if constexpr (PP) {
+    // F_mm' (times 2 pi M, folded into V) with the half-sample phase, zero-padded to N
+    C<T>* f = fft_pp<T>(buf, buf + N, fM, twM, false);
+    C<T>* x = (f == buf) ? buf + N : buf;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
+      x[k] = (mp == 0x7fffffff) ? mkc<T>(0, 0) : cmul<T>(f[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    C<T>* y = fft_pp<T>(x, f, fN, twN, true);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) y[k] = cmul<T>(y[k], V[k]);
+    __syncthreads();
+    res = fft_pp<T>(y, (y == buf) ? buf + N : buf, fN, twN, false);
+  } else {
+    fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+    C<T> v[kFftVPT];
 #pragma unroll
-  for (int r = 0; r < kFftVPT; ++r) {
-    const int k = threadIdx.x + r * blockDim.x;
-    if (k < N) buf[k] = v[r];
+    for (int r = 0; r < kFftVPT; ++r) {
+      const int k = threadIdx.x + r * blockDim.x;
+      if (k < N) {
+        int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
+        if (mp == 0x7fffffff) v[r] = mkc<T>(0, 0);
+        else v[r] = cmul<T>(buf[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFftVPT; ++r) {
+      const int k = threadIdx.x + r * blockDim.x;
+      if (k < N) buf[k] = v[r];
+    }
+    __syncthreads();
+    fft_inplace<T, kFftVPT>(buf, fN, twN, true);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmul<T>(buf[k], V[k]);
+    __syncthreads();
+    fft_inplace<T, kFftVPT>(buf, fN, twN, false);
+    res = buf;
   }
-  __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fN, twN, true);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmul<T>(buf[k], V[k]);
-  __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fN, twN, false);
   // fold m' >= 0: G+_{m,0} = G_m0, G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'}
   C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    C<T> a = buf[mp];
+    C<T> a = res[mp];
     if (mp > 0) {
-      const C<T> c = buf[N - mp];
+      const C<T> c = res[N - mp];
       a.x += sg * c.x;
       a.y += sg * c.y;
     }
@@ -183,9 +199,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDes
     buf[k] = cmulc<T>(y, phase[mp + L - 1]);
   }
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, true);
   C<T>* out = Gt + (long long)b * L * M;
-  for (int t = threadIdx.x; t < L; t += blockDim.x) out[(long long)t * M + im] = buf[t];
+  for (int t = threadIdx.x; t < L; t += blockDim.x) out[(long long)t * M + im] = res[t];
 }
 
 template <typename T>
@@ -201,19 +217,19 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc 
     buf[k] = in[m + L - 1];
   }
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, true);
   double2* f = map + (long long)b * d.nmw;
   if (t < L - 1) {
-    for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(buf[p]);
+    for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(res[p]);
   } else if (threadIdx.x == 0) {
-    f[(long long)(L - 1) * M] = to64(buf[0]);
+    f[(long long)(L - 1) * M] = to64(res[0]);
   }
 }
 
 // --------------------------------------------------------------------------
 // adjoint of the forward: Wigner^H (run_wigner mode 1) -> theta_forward^H -> phi_forward^H
 // --------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool PP>
 __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
                                         const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
                                         const C<T>* __restrict__ V, const double2* __restrict__ Gp,
@@ -236,35 +252,51 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d
     buf[k] = mul_ipow<T>(from64<T>(in[a]), q);
   }
   __syncthreads();
-  // convolution^H: zero-pad, inverse DFT, times conj(V), DFT
-  fft_inplace<T, kFftVPT>(buf, fN, twN, true);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmulc<T>(buf[k], V[k]);
-  __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fN, twN, false);
-  // theta-DFT^H: F^H_{m,m''} e^{+i m'' pi/M} placed on the length-M grid, inverse DFT
-  C<T> v[kFftVPT];
-#pragma unroll
-  for (int r = 0; r < kFftVPT; ++r) {
-    const int k = threadIdx.x + r * blockDim.x;
-    if (k < M) {
+  // convolution^H: zero-pad, inverse DFT, times conj(V), DFT; then the theta-DFT^H:
+  // F^H_{m,m''} e^{+i m'' pi/M} placed on the length-M grid, inverse DFT
+  C<T>* res;
+  if constexpr (PP) {
+    C<T>* y = fft_pp<T>(buf, buf + N, fN, twN, true);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) y[k] = cmulc<T>(y[k], V[k]);
+    __syncthreads();
+    C<T>* z = fft_pp<T>(y, (y == buf) ? buf + N : buf, fN, twN, false);
+    C<T>* x = (z == buf) ? buf + N : buf;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
       const int mp = (k <= L - 1) ? k : k - M;
-      v[r] = cmulc<T>(buf[mp < 0 ? mp + N : mp], phase[mp + L - 1]);
+      x[k] = cmulc<T>(z[mp < 0 ? mp + N : mp], phase[mp + L - 1]);
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    res = fft_pp<T>(x, z, fM, twM, true);
+  } else {
+    fft_inplace<T, kFftVPT>(buf, fN, twN, true);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmulc<T>(buf[k], V[k]);
+    __syncthreads();
+    fft_inplace<T, kFftVPT>(buf, fN, twN, false);
+    C<T> v[kFftVPT];
 #pragma unroll
-  for (int r = 0; r < kFftVPT; ++r) {
-    const int k = threadIdx.x + r * blockDim.x;
-    if (k < M) buf[k] = v[r];
+    for (int r = 0; r < kFftVPT; ++r) {
+      const int k = threadIdx.x + r * blockDim.x;
+      if (k < M) {
+        const int mp = (k <= L - 1) ? k : k - M;
+        v[r] = cmulc<T>(buf[mp < 0 ? mp + N : mp], phase[mp + L - 1]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFftVPT; ++r) {
+      const int k = threadIdx.x + r * blockDim.x;
+      if (k < M) buf[k] = v[r];
+    }
+    __syncthreads();
+    fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+    res = buf;
   }
-  __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
   // extension^H: G^H(t) = G~^H(t) + (-1)^(m+s) G~^H(2L-2-t) for t <= L-2
   C<T>* out = Gt + (long long)b * L * M;
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    C<T> a = buf[t];
+    C<T> a = res[t];
     if (t <= L - 2) {
-      const C<T> c = buf[2 * L - 2 - t];
+      const C<T> c = res[2 * L - 2 - t];
       a.x += (T)sg * c.x;
       a.y += (T)sg * c.y;
     }
@@ -293,9 +325,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, 
     buf[k] = in[m + L - 1];
   }
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, true);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, true);
   const T sc = (T)(2.0 * M_PI / M);
-  for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(cscale<T>(buf[p], sc));
+  for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(cscale<T>(res[p], sc));
 }
 
 // --------------------------------------------------------------------------
@@ -317,10 +349,10 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse_adjoint(Dims d, 
   }
   for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = from64<T>(f[(long long)t * M + p]);
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, false);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     const int m = i - (L - 1);
-    out[(long long)i * L + t] = buf[m < 0 ? m + M : m];
+    out[(long long)i * L + t] = res[m < 0 ? m + M : m];
   }
 }
 
@@ -338,13 +370,13 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse_adjoint(Dims d
   const C<T>* g = Gt + ((long long)b * M + im) * L;
   for (int t = threadIdx.x; t < M; t += blockDim.x) buf[t] = (t < L) ? g[t] : mkc<T>(0, 0);
   __syncthreads();
-  fft_inplace<T, kFftVPT>(buf, fM, twM, false);
+  const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, false);
   // F^H_mm' = e^{-i m' pi/M} DFT[m'], folded for the Wigner stage
   C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    C<T> a = cmul<T>(buf[mp], phase[mp + L - 1]);
+    C<T> a = cmul<T>(res[mp], phase[mp + L - 1]);
     if (mp > 0) {
-      const C<T> c = cmul<T>(buf[M - mp], phase[-mp + L - 1]);
+      const C<T> c = cmul<T>(res[M - mp], phase[-mp + L - 1]);
       a.x += sg * c.x;
       a.y += sg * c.y;
     }
@@ -389,9 +421,6 @@ __global__ void k_pole_forward_adjoint(Dims d, const double2* __restrict__ Gp, c
   }
 }
 
-template <typename T>
-int smem_bytes(int n) { return n * (int)sizeof(C<T>); }
-
 template <typename K>
 cudaError_t set_smem(K kernel, int bytes) {
   if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -405,83 +434,109 @@ Dims dims_of(const mw_plan* p) {
   return d;
 }
 
-int threads_for(int n) {
+// block size of the ping-pong kernels (any size works; a multiple of 32 up to 512)
+int threads_pp(int n) {
+  int t = (n + 3) / 4;
+  t = ((t + 31) / 32) * 32;
+  return t < 32 ? 32 : (t > kFftMaxThreads ? kFftMaxThreads : t);
+}
+// block size of the in-place kernels: kFftVPT * threads >= n
+int threads_inplace(int n) {
   int t = (n + kFftVPT - 1) / kFftVPT;
   t = ((t + 31) / 32) * 32;
   return t < 32 ? 32 : t;
 }
+constexpr int kSmemMax = 232448;
+
+template <typename T> int pp_bytes(int n) { return 2 * n * (int)sizeof(C<T>); }
 
 template <typename T>
 cudaError_t phi_forward_t(const mw_plan* p, const double2* map, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_phi_forward<T>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_forward<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+  k_phi_forward<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t theta_forward_t(const mw_plan* p, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->N);
-  cudaError_t e = set_smem(k_theta_forward<T>, sm);
-  if (e != cudaSuccess) return e;
-  k_theta_forward<T><<<dim3(p->M, p->B), threads_for(p->N), sm, st>>>(
-      dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
-      (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
+  cudaError_t e;
+  if (pp_bytes<T>(p->N) <= kSmemMax) {
+    const int sm = pp_bytes<T>(p->N);
+    if ((e = set_smem(k_theta_forward<T, true>, sm)) != cudaSuccess) return e;
+    k_theta_forward<T, true><<<dim3(p->M, p->B), threads_pp(p->N), sm, st>>>(
+        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+        (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
+  } else {
+    const int sm = p->N * (int)sizeof(C<T>);
+    if ((e = set_smem(k_theta_forward<T, false>, sm)) != cudaSuccess) return e;
+    k_theta_forward<T, false><<<dim3(p->M, p->B), threads_inplace(p->N), sm, st>>>(
+        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+        (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
+  }
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t theta_inverse_t(const mw_plan* p, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_theta_inverse<T>, sm);
   if (e != cudaSuccess) return e;
-  k_theta_inverse<T><<<dim3(p->M, p->B), threads_for(p->M), sm, st>>>(
+  k_theta_inverse<T><<<dim3(p->M, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t phi_inverse_t(const mw_plan* p, double2* map, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_phi_inverse<T>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_inverse<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+  k_phi_inverse<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t theta_forward_adjoint_t(const mw_plan* p, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->N);
-  cudaError_t e = set_smem(k_theta_forward_adjoint<T>, sm);
-  if (e != cudaSuccess) return e;
-  k_theta_forward_adjoint<T><<<dim3(p->M, p->B), threads_for(p->N), sm, st>>>(
-      dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
-      (const C<T>*)p->d_V, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
+  cudaError_t e;
+  if (pp_bytes<T>(p->N) <= kSmemMax) {
+    const int sm = pp_bytes<T>(p->N);
+    if ((e = set_smem(k_theta_forward_adjoint<T, true>, sm)) != cudaSuccess) return e;
+    k_theta_forward_adjoint<T, true><<<dim3(p->M, p->B), threads_pp(p->N), sm, st>>>(
+        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+        (const C<T>*)p->d_V, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
+  } else {
+    const int sm = p->N * (int)sizeof(C<T>);
+    if ((e = set_smem(k_theta_forward_adjoint<T, false>, sm)) != cudaSuccess) return e;
+    k_theta_forward_adjoint<T, false><<<dim3(p->M, p->B), threads_inplace(p->N), sm, st>>>(
+        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
+        (const C<T>*)p->d_V, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
+  }
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t phi_forward_adjoint_t(const mw_plan* p, double2* map, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_phi_forward_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_forward_adjoint<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+  k_phi_forward_adjoint<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t phi_inverse_adjoint_t(const mw_plan* p, const double2* map, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_phi_inverse_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_inverse_adjoint<T><<<dim3(p->L, p->B), threads_for(p->M), sm, st>>>(
+  k_phi_inverse_adjoint<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t theta_inverse_adjoint_t(const mw_plan* p, cudaStream_t st) {
-  const int sm = smem_bytes<T>(p->M);
+  const int sm = pp_bytes<T>(p->M);
   cudaError_t e = set_smem(k_theta_inverse_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
-  k_theta_inverse_adjoint<T><<<dim3(p->M, p->B), threads_for(p->M), sm, st>>>(
+  k_theta_inverse_adjoint<T><<<dim3(p->M, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp,
       p->d_spins);
   return cudaGetLastError();

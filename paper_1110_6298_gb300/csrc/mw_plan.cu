@@ -20,11 +20,12 @@ void unit_root(long long x, long long n, double* re, double* im) {
   *im = (double)-sinl(a);
 }
 
-// Radix sequence of n: 4s, then 2, 3, 5, 7, then any remaining odd primes.
+// Radix sequence of n: 8s, 4s, then 2, 3, 5, 7, then any remaining odd primes.
 bool factorize(int n, FftDesc* d) {
   d->n = n;
   d->nrad = 0;
   int r = n;
+  while (r % 8 == 0) { d->rad[d->nrad++] = 8; r /= 8; }
   while (r % 4 == 0) { d->rad[d->nrad++] = 4; r /= 4; }
   while (r % 2 == 0) { d->rad[d->nrad++] = 2; r /= 2; }
   for (int p = 3; r > 1; p += 2) {
