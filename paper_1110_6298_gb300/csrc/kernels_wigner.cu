@@ -23,6 +23,7 @@
 // reads Delta_{m'm} from row |m| of the quarter plane through the transpose
 // symmetry, so every access is a contiguous row segment.
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -53,53 +54,51 @@ __device__ __forceinline__ float to_f32_int(double v) {
 // Persistent Risbo sweep over the planes l in [l_begin, l_end) of one chunk.
 //
 // One cooperative launch per chunk; a grid-wide barrier (bounded spin) separates
-// the half steps.  Each half step computes only the lower triangle b <= a of the
-// new quarter plane in 32 x 32 tiles (the transpose symmetry supplies the rest),
-// staging the old plane's tile plus a one-element halo in shared memory.  Per
-// element the stencil costs 6 FP64 instructions: with pre-scaled column factors
-// cn = sqrt(j'-nu)/(2 sqrt2 j') and cp = sqrt(j'+nu)/(2 sqrt2 j'),
+// consecutive l.  Each l is one pass over 32 x 32 tiles of the lower triangle
+// b <= a of the new quarter plane (the transpose symmetry supplies the rest):
+// a tile stages the previous integer plane Delta^{l-1} on rows/columns
+// a0-1 .. a0+32 in shared memory, computes the half-integer plane d^{l-1/2} on
+// rows/columns a0-1 .. a0+31 (including the index -1, i.e. m = -1/2, directly
+// from the gather formula) and from it the integer plane Delta^l on the tile.
+// Recomputing the 33 x 33 half plane per tile costs 6% more FP64 work than a
+// global half step but saves a grid barrier and the half plane's memory
+// traffic per l.  Per element the stencil costs 6 FP64 instructions: with the
+// column factors cn = sqrt(j'-nu)/(2 sqrt2 j'), cp = sqrt(j'+nu)/(2 sqrt2 j')
+// kept in shared memory,
 //   e = cn (sqrt(j'-mu) d_{+,+} - sqrt(j'+mu) d_{-,+}) + cp (sqrt(j'-mu) d_{+,-} + sqrt(j'+mu) d_{-,-}).
 // Integer planes are also written out as full quarters where a contraction
 // reads them (FP32 staging copy on the mixed path; the FP64 plane itself on the
 // FP64 path), the upper triangle through an in-shared-memory transpose.
 // ---------------------------------------------------------------------------
 constexpr int kRT = 32;         // tile edge
-constexpr int kRThreads = 256;  // 32 x 8 threads, 4 rows each
+constexpr int kRThreads = 256;  // 32 x 8 threads
 constexpr unsigned kBarrierPolls = 1u << 24;
 
 struct RisboArgs {
   double* S;          // FP64 integer planes; plane l at slot l % nslot
   int nslot;
-  double* H;          // half-integer plane
   float* S32;         // FP32 staging of the integer planes (slot l - l0), or null
   int l0;
   int full64;         // write transposed tiles into the FP64 integer plane
   int LD;
-  const double* sq;   // sqrt(k)
+  const double* sq;      // sqrt(k)
   const double* rscale;  // 1 / (sqrt2 two_jp)
   unsigned* bar;      // grid barrier counter (zeroed before the launch)
   int* err;
 };
 
-// Old-plane value d[i][k] (indices of the quarter storage, possibly -1 or above
-// the diagonal), through the pi/2 symmetries; zero beyond the plane.
-__device__ __forceinline__ double old_val(const double* __restrict__ d, int LD, int i, int k, int nold, int jo2) {
-  if (i >= nold || k >= nold) return 0.0;
-  int ex = 0;  // the value is (-1)^ex d[i][k]
-  if (i < 0) {  // d_{-1/2, n} = (-1)^(j - n) d_{1/2, n}
-    const int n2 = (k < 0) ? -1 : 2 * k + 1;
-    ex += (jo2 - n2) / 2;
-    i = 0;
-  }
-  if (k < 0) {  // d_{m, -1/2} = (-1)^(j + m) d_{m, 1/2}
-    ex += (jo2 + 2 * i + 1) / 2;
-    k = 0;
-  }
-  if (k > i) {  // d_{mn} = (-1)^(m-n) d_{nm}
-    ex += i - k;
-    const int t = i; i = k; k = t;
-  }
-  return flip_sign(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks in the last half step
+// Value of the integer plane Delta^{l-1} (j = l-1, quarter storage, lower
+// triangle valid) at quarter indices (i, k), which may be -1 or above the
+// diagonal: index -1 is m = -1 and reflects to +1 through
+//   d_{-m,n} = (-1)^(j-n) d_{mn}, d_{m,-n} = (-1)^(j+m) d_{mn}  (Eq. wignerd_sym2 at pi/2, sym1),
+// and the upper triangle is read through d_{mn} = (-1)^(m-n) d_{nm}.
+__device__ __forceinline__ double prev_val(const double* __restrict__ d, int LD, int i, int k, int j) {
+  int ex = 0;  // value = (-1)^ex d[i][k]
+  if (i < 0) { ex += j - k; i = -i; }
+  if (k < 0) { ex += j + i; k = -k; }
+  if (i > j || k > j) return 0.0;
+  if (k > i) { ex += i - k; const int t = i; i = k; k = t; }
+  return flip_sign(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks for the last l
 }
 
 // Grid-wide barrier for a cooperative launch; gives up after kBarrierPolls polls,
@@ -130,78 +129,92 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned& gen, int* err
 }
 
 __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
-  __shared__ double halo[kRT + 2][kRT + 3];
+  __shared__ double dh[kRT + 2][kRT + 3];   // Delta^{l-1} on rows/cols a0-1 .. a0+32
+  __shared__ double hh[kRT + 1][kRT + 2];   // d^{l-1/2} on rows/cols a0-1 .. a0+31
   __shared__ double tr[kRT][kRT + 1];
+  __shared__ double colf[4][kRT + 1];       // cn, cp of the half plane (33 cols) and of the integer plane (32)
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int LD = A.LD;
   const size_t plane = (size_t)LD * LD;
   unsigned gen = 0;
   for (int l = l_begin; l < l_end; ++l) {
-    for (int h = 0; h < 2; ++h) {
-      const int two_jp = 2 * l - 1 + h;
-      const int odd = two_jp & 1;
-      const int nnew = odd ? (two_jp + 1) / 2 : two_jp / 2 + 1;
-      const int nold = (two_jp + 1) / 2;
-      const int jo2 = two_jp - 1;
-      const double* d = (h == 0) ? A.S + (size_t)((l - 1) % A.nslot) * plane : A.H;
-      double* e = (h == 0) ? A.H : A.S + (size_t)(l % A.nslot) * plane;
-      float* st = (h == 1 && A.S32) ? A.S32 + (size_t)(l - A.l0) * plane : nullptr;
-      const bool full64 = (h == 1) && A.full64;
-      const double sc = A.rscale[two_jp];  // table: an FP64 division per thread is expensive here
-      const int T = (nnew + kRT - 1) / kRT;
-      const int ntiles = T * (T + 1) / 2;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-        while (I * (I + 1) / 2 > t) --I;
-        while ((I + 1) * (I + 2) / 2 <= t) ++I;
-        const int J = t - I * (I + 1) / 2;
-        const int a0 = I * kRT, b0 = J * kRT;
-        for (int idx = tid; idx < (kRT + 2) * (kRT + 2); idx += kRThreads) {
-          const int r = idx / (kRT + 2), c = idx % (kRT + 2);
-          halo[r][c] = old_val(d, LD, a0 - 1 + r, b0 - 1 + c, nold, jo2);
+    const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
+    const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
+    const double* d = A.S + (size_t)((l - 1) % A.nslot) * plane;
+    double* e = A.S + (size_t)(l % A.nslot) * plane;
+    float* st = A.S32 ? A.S32 + (size_t)(l - A.l0) * plane : nullptr;
+    const double sch = A.rscale[th], sci = A.rscale[ti];
+    const int T = (nnew + kRT - 1) / kRT;
+    const int ntiles = T * (T + 1) / 2;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while (I * (I + 1) / 2 > t) --I;
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      const int J = t - I * (I + 1) / 2;
+      const int a0 = I * kRT, b0 = J * kRT;
+      for (int idx = tid; idx < (kRT + 2) * (kRT + 2); idx += kRThreads) {
+        const int r = idx / (kRT + 2), c = idx % (kRT + 2);
+        dh[r][c] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+      }
+      if (tid < kRT + 1) {  // half-plane column factors, columns k = b0-1 .. b0+31 (nu = k + 1/2)
+        const int nu2 = 2 * (b0 - 1 + tid) + 1;
+        const bool in = (b0 - 1 + tid) < nh;
+        colf[0][tid] = in ? sch * A.sq[(th - nu2) / 2] : 0.0;
+        colf[1][tid] = in ? sch * A.sq[(th + nu2) / 2] : 0.0;
+      } else if (tid >= 64 && tid < 64 + kRT) {  // integer-plane column factors, b = b0 .. b0+31
+        const int b = b0 + tid - 64;
+        const bool in = b < nnew;
+        colf[2][tid - 64] = in ? sci * A.sq[(ti - 2 * b) / 2] : 0.0;
+        colf[3][tid - 64] = in ? sci * A.sq[(ti + 2 * b) / 2] : 0.0;
+      }
+      __syncthreads();
+      // half plane on (i, k) = (a0-1+r, b0-1+c), r, c < 33; old indices i+1 and i (offset 0 -> 1/2)
+      for (int idx = tid; idx < (kRT + 1) * (kRT + 1); idx += kRThreads) {
+        const int r = idx / (kRT + 1), c = idx % (kRT + 1);
+        const int i = a0 - 1 + r, k = b0 - 1 + c;
+        double v = 0.0;
+        if (i < nh && k < nh) {
+          const int mu2 = 2 * i + 1;
+          const double cmm = A.sq[(th - mu2) / 2], cpm = A.sq[(th + mu2) / 2];
+          const double t1 = fma(-cpm, dh[r][c + 1], cmm * dh[r + 1][c + 1]);
+          const double t2 = fma(cpm, dh[r][c], cmm * dh[r + 1][c]);
+          v = fma(colf[1][c], t2, colf[0][c] * t1);
         }
+        hh[r][c] = v;
+      }
+      __syncthreads();
+      // integer plane on the tile; half-plane indices a and a-1 -> hh rows r+1 and r
+      const bool need_tr = (J < I) && (st || A.full64);
+#pragma unroll
+      for (int q = 0; q < kRT / 8; ++q) {
+        const int r = ty + 8 * q;
+        const int a = a0 + r, b = b0 + tx;
+        double v = 0.0;
+        if (a < nnew && b < nnew) {
+          const double cmm = A.sq[(ti - 2 * a) / 2], cpm = A.sq[(ti + 2 * a) / 2];
+          const double t1 = fma(-cpm, hh[r][tx + 1], cmm * hh[r + 1][tx + 1]);
+          const double t2 = fma(cpm, hh[r][tx], cmm * hh[r + 1][tx]);
+          v = fma(colf[3][tx], t2, colf[2][tx] * t1);
+          e[(size_t)a * LD + b] = v;
+          if (st) st[(size_t)a * LD + b] = to_f32_int(v);
+        }
+        if (need_tr) tr[r][tx] = v;
+      }
+      if (need_tr) {
         __syncthreads();
-        const int b = b0 + tx;
-        const int nu2 = 2 * b + odd;
-        const bool bok = b < nnew;
-        const double cn = bok ? sc * A.sq[(two_jp - nu2) / 2] : 0.0;
-        const double cp = bok ? sc * A.sq[(two_jp + nu2) / 2] : 0.0;
-        const bool need_tr = (J < I) && (st || full64);
 #pragma unroll
         for (int q = 0; q < kRT / 8; ++q) {
-          const int r = ty + 8 * q;
-          const int a = a0 + r;
-          double v = 0.0;
-          if (a < nnew && bok) {
-            const int mu2 = 2 * a + odd;
-            const double cmm = A.sq[(two_jp - mu2) / 2], cpm = A.sq[(two_jp + mu2) / 2];
-            const double dpp = halo[r + 1 + odd][tx + 1 + odd], dmp = halo[r + odd][tx + 1 + odd];
-            const double dpm = halo[r + 1 + odd][tx + odd], dmm = halo[r + odd][tx + odd];
-            const double t1 = fma(-cpm, dmp, cmm * dpp);
-            const double t2 = fma(cpm, dmm, cmm * dpm);
-            v = fma(cp, t2, cn * t1);
-            e[(size_t)a * LD + b] = v;
-            if (st) st[(size_t)a * LD + b] = to_f32_int(v);
-          }
-          if (need_tr) tr[r][tx] = v;
-        }
-        if (need_tr) {
-          __syncthreads();
-#pragma unroll
-          for (int q = 0; q < kRT / 8; ++q) {
-            const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
-            if (aa < nnew && bb < nnew) {
-              const double v = flip_sign(tr[tx][ty + 8 * q], aa - bb);
-              if (full64) e[(size_t)bb * LD + aa] = v;
-              if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
-            }
+          const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
+          if (aa < nnew && bb < nnew) {
+            const double v = flip_sign(tr[tx][ty + 8 * q], aa - bb);
+            if (A.full64) e[(size_t)bb * LD + aa] = v;
+            if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
           }
         }
-        __syncthreads();
       }
-      const bool last = (l == l_end - 1) && (h == 1);
-      if (!last && !grid_sync(A.bar, gen, A.err)) return;
+      __syncthreads();
     }
+    if (l < l_end - 1 && !grid_sync(A.bar, gen, A.err)) return;
   }
 }
 
@@ -359,7 +372,7 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
   cudaError_t e = cudaMemsetAsync(p->d_bar, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   RisboArgs a;
-  a.S = S; a.nslot = nslot; a.H = p->d_H; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
+  a.S = S; a.nslot = nslot; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
   a.sq = p->d_sqrt; a.rscale = p->d_rscale; a.bar = p->d_bar; a.err = p->d_err;
   void* args[] = {&a, &lb, &le};
   e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args, 0, st);
@@ -440,13 +453,20 @@ cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double
 
 }  // namespace
 
+// Co-resident blocks per SM of the persistent recursion kernel: the occupancy
+// limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 2, the fastest measured).
 int risbo_blocks_per_sm() {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
-  return n < 1 ? 1 : (n > 4 ? 4 : n);
+  int cap = 2;
+  if (const char* env = getenv("MW_RISBO_BLOCKS_PER_SM")) {
+    const int v = atoi(env);
+    if (v >= 1 && v <= 32) cap = v;
+  }
+  return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
 cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
