@@ -57,7 +57,7 @@ struct mw_plan {
                                    // mixed path: [2][LD][LD] ping-pong recursion state
   float* d_S32 = nullptr;          // mixed path: [kTcChunk][LD][LD] FP32 copies of the integer planes
   int* d_err = nullptr;            // device error word (bit 0: tensor-core wait, bit 1: grid barrier)
-  unsigned* d_bar = nullptr;       // grid-barrier counter of the persistent Risbo kernel
+  int* d_prog = nullptr;           // per-tile progress counters of the persistent Risbo kernel
   int risbo_grid = 0;              // co-resident blocks of the persistent Risbo kernel
   double* d_H = nullptr;           // [LD][LD] half-integer plane
   int LD = 0;                      // plane row stride (L+1)

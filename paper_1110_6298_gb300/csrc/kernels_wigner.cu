@@ -83,7 +83,7 @@ struct RisboArgs {
   int LD;
   const double* sq;      // sqrt(k)
   const double* rscale;  // 1 / (sqrt2 two_jp)
-  unsigned* bar;      // grid barrier counter (zeroed before the launch)
+  int* prog;          // per-tile progress: last plane l published
   int* err;
 };
 
@@ -101,42 +101,42 @@ __device__ __forceinline__ double prev_val(const double* __restrict__ d, int LD,
   return flip_sign(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks for the last l
 }
 
-// Grid-wide barrier for a cooperative launch; gives up after kBarrierPolls polls,
-// records the timeout in *err and returns false (every block then leaves).
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned& gen, int* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    gen += 1;
-    const unsigned target = gen * gridDim.x;
-    __threadfence();
-    atomicAdd(bar, 1u);
-    int ok = 1;
-    unsigned polls = 0;
-    while (true) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if (v >= target) break;
-      if (++polls > kBarrierPolls) { ok = 0; atomicOr(err, 2); break; }
-      __nanosleep(20);
-    }
-    __threadfence();
-    if (ok && *(volatile int*)err) ok = 0;
-    s_ok = ok;
+// Tile (I, J), J <= I, of the lower triangle has linear index I (I+1)/2 + J.
+__device__ __forceinline__ int tile_index(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// Wait until tile t has published step `step` (bounded; returns false on timeout).
+__device__ __forceinline__ bool wait_tile(const int* prog, int t, int step) {
+  for (unsigned polls = 0; polls < kBarrierPolls; ++polls) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(prog + t) : "memory");
+    if (v >= step) return true;
+    __nanosleep(32);
   }
-  __syncthreads();
-  return s_ok != 0;
+  return false;
 }
 
+__global__ void k_prog_init(int* prog, int n, int value) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) prog[i] = value;
+}
+
+// Dataflow scheduling: block c owns the tiles t = c, c + G, ... and processes
+// (l, t) in increasing (l, t) order; before computing tile (I, J) of plane l it
+// waits until the tiles of plane l-1 that its halo reads -- block rows I-1..I+1
+// and columns J-1..J+1, mapped into the lower triangle -- have published l-1,
+// then publishes l itself.  Every block follows the same global order and the
+// launch is cooperative (all blocks co-resident), so every wait ends; a wait
+// that exceeds its poll limit records the timeout and the block leaves.  A
+// block that overwrites plane l-2 (two-plane ping-pong) does so only after all
+// readers of that region -- its neighbours at step l-1 -- have finished.
 __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
   __shared__ double dh[kRT + 2][kRT + 3];   // Delta^{l-1} on rows/cols a0-1 .. a0+32
-  __shared__ double hh[kRT + 1][kRT + 2];   // d^{l-1/2} on rows/cols a0-1 .. a0+31
+  __shared__ double hh[kRT + 1][kRT + 1];   // d^{l-1/2} on rows/cols a0-1 .. a0+31 (odd row stride)
   __shared__ double tr[kRT][kRT + 1];
   __shared__ double colf[4][kRT + 1];       // cn, cp of the half plane (33 cols) and of the integer plane (32)
+  __shared__ int s_ok;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int LD = A.LD;
   const size_t plane = (size_t)LD * LD;
-  unsigned gen = 0;
   for (int l = l_begin; l < l_end; ++l) {
     const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
     const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
     double* e = A.S + (size_t)(l % A.nslot) * plane;
     float* st = A.S32 ? A.S32 + (size_t)(l - A.l0) * plane : nullptr;
     const double sch = A.rscale[th], sci = A.rscale[ti];
-    const int T = (nnew + kRT - 1) / kRT;
+    const int T = (nnew + kRT - 1) / kRT;       // tile rows of plane l
+    const int Tp = (l + kRT - 1) / kRT;         // tile rows of plane l-1 (size l)
     const int ntiles = T * (T + 1) / 2;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -152,6 +153,22 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
       while ((I + 1) * (I + 2) / 2 <= t) ++I;
       const int J = t - I * (I + 1) / 2;
       const int a0 = I * kRT, b0 = J * kRT;
+      if (tid == 0) {
+        int ok = 1;
+        if (l > l_begin) {
+          for (int di = -1; di <= 1 && ok; ++di)
+            for (int dj = -1; dj <= 1 && ok; ++dj) {
+              const int Ii = I + di, Jj = J + dj;
+              if (Ii < 0 || Jj < 0 || Ii >= Tp || Jj >= Tp) continue;  // not part of plane l-1
+              const int hi = Ii > Jj ? Ii : Jj, lo = Ii > Jj ? Jj : Ii;
+              if (!wait_tile(A.prog, tile_index(hi, lo), l - 1)) { ok = 0; atomicOr(A.err, 2); }
+            }
+        }
+        if (ok && *(volatile int*)A.err) ok = 0;
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) return;
       for (int idx = tid; idx < (kRT + 2) * (kRT + 2); idx += kRThreads) {
         const int r = idx / (kRT + 2), c = idx % (kRT + 2);
         dh[r][c] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
@@ -168,40 +185,65 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
         colf[3][tid - 64] = in ? sci * A.sq[(ti + 2 * b) / 2] : 0.0;
       }
       __syncthreads();
-      // half plane on (i, k) = (a0-1+r, b0-1+c), r, c < 33; old indices i+1 and i (offset 0 -> 1/2)
-      for (int idx = tid; idx < (kRT + 1) * (kRT + 1); idx += kRThreads) {
-        const int r = idx / (kRT + 1), c = idx % (kRT + 1);
-        const int i = a0 - 1 + r, k = b0 - 1 + c;
-        double v = 0.0;
-        if (i < nh && k < nh) {
-          const int mu2 = 2 * i + 1;
-          const double cmm = A.sq[(th - mu2) / 2], cpm = A.sq[(th + mu2) / 2];
-          const double t1 = fma(-cpm, dh[r][c + 1], cmm * dh[r + 1][c + 1]);
-          const double t2 = fma(cpm, dh[r][c], cmm * dh[r + 1][c]);
-          v = fma(colf[1][c], t2, colf[0][c] * t1);
+      // half plane on (i, k) = (a0-1+r, b0-1+c), r, c < 33; old indices i+1 and i.
+      // Row segments: the product sqrt(j'-mu) d_{+,jp} of column c is the
+      // sqrt(j'-mu) d_{+,jm} of column c+1, so it is carried along (5 FP64
+      // instructions per element).
+      for (int task = tid; task < (kRT + 1) * 4; task += kRThreads) {
+        const int r = task % (kRT + 1), seg = task / (kRT + 1);
+        const int c0 = seg * 9, c1 = min(c0 + 9, kRT + 1);  // 9, 9, 9, 6 columns
+        const int i = a0 - 1 + r;
+        if (i >= nh) {
+          for (int c = c0; c < c1; ++c) hh[r][c] = 0.0;
+          continue;
         }
-        hh[r][c] = v;
+        const int mu2 = 2 * i + 1;
+        const double cmm = A.sq[(th - mu2) / 2], cpm = A.sq[(th + mu2) / 2];
+        double pprev = cmm * dh[r + 1][c0];
+        for (int c = c0; c < c1; ++c) {
+          const double p = cmm * dh[r + 1][c + 1];
+          const double t1 = fma(-cpm, dh[r][c + 1], p);
+          const double t2 = fma(cpm, dh[r][c], pprev);
+          hh[r][c] = (b0 - 1 + c < nh) ? fma(colf[1][c], t2, colf[0][c] * t1) : 0.0;
+          pprev = p;
+        }
       }
       __syncthreads();
-      // integer plane on the tile; half-plane indices a and a-1 -> hh rows r+1 and r
+      // integer plane on the tile into shared memory (half-plane indices a and a-1
+      // -> hh rows r+1 and r; row segments of 4 columns carry the shared product),
+      // then coalesced stores of the tile and, where needed, of its transpose
       const bool need_tr = (J < I) && (st || A.full64);
+      {
+        const int r = tid & 31, seg = tid >> 5;  // 32 rows x 8 segments of 4 columns
+        const int a = a0 + r, c0 = seg * 4;
+        if (a < nnew) {
+          const double cmm = A.sq[(ti - 2 * a) / 2], cpm = A.sq[(ti + 2 * a) / 2];
+          double pprev = cmm * hh[r + 1][c0];
+#pragma unroll
+          for (int c = c0; c < c0 + 4; ++c) {
+            const double p = cmm * hh[r + 1][c + 1];
+            const double t1 = fma(-cpm, hh[r][c + 1], p);
+            const double t2 = fma(cpm, hh[r][c], pprev);
+            pprev = p;
+            tr[r][c] = fma(colf[3][c], t2, colf[2][c] * t1);
+          }
+        } else {
+#pragma unroll
+          for (int c = c0; c < c0 + 4; ++c) tr[r][c] = 0.0;
+        }
+      }
+      __syncthreads();
 #pragma unroll
       for (int q = 0; q < kRT / 8; ++q) {
         const int r = ty + 8 * q;
         const int a = a0 + r, b = b0 + tx;
-        double v = 0.0;
         if (a < nnew && b < nnew) {
-          const double cmm = A.sq[(ti - 2 * a) / 2], cpm = A.sq[(ti + 2 * a) / 2];
-          const double t1 = fma(-cpm, hh[r][tx + 1], cmm * hh[r + 1][tx + 1]);
-          const double t2 = fma(cpm, hh[r][tx], cmm * hh[r + 1][tx]);
-          v = fma(colf[3][tx], t2, colf[2][tx] * t1);
+          const double v = tr[r][tx];
           e[(size_t)a * LD + b] = v;
           if (st) st[(size_t)a * LD + b] = to_f32_int(v);
         }
-        if (need_tr) tr[r][tx] = v;
       }
       if (need_tr) {
-        __syncthreads();
 #pragma unroll
         for (int q = 0; q < kRT / 8; ++q) {
           const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
@@ -212,9 +254,12 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
           }
         }
       }
-      __syncthreads();
+      __syncthreads();  // all writes of the tile issued
+      if (tid == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(A.prog + t), "r"(l) : "memory");
+      }
     }
-    if (l < l_end - 1 && !grid_sync(A.bar, gen, A.err)) return;
   }
 }
 
@@ -369,11 +414,13 @@ namespace {
 cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, int full64, int lb, int le,
                          cudaStream_t st, int* nd) {
   if (lb >= le) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(p->d_bar, 0, sizeof(unsigned), st);
+  const int Tm = (le + kRT - 1) / kRT;
+  k_prog_init<<<8, 256, 0, st>>>(p->d_prog, Tm * (Tm + 1) / 2, lb - 1);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   RisboArgs a;
   a.S = S; a.nslot = nslot; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
-  a.sq = p->d_sqrt; a.rscale = p->d_rscale; a.bar = p->d_bar; a.err = p->d_err;
+  a.sq = p->d_sqrt; a.rscale = p->d_rscale; a.prog = p->d_prog; a.err = p->d_err;
   void* args[] = {&a, &lb, &le};
   e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args, 0, st);
   if (nd) *nd += 1;
@@ -454,14 +501,14 @@ cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double
 }  // namespace
 
 // Co-resident blocks per SM of the persistent recursion kernel: the occupancy
-// limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 2, the fastest measured).
+// limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 4, the fastest measured).
 int risbo_blocks_per_sm() {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
-  int cap = 2;
+  int cap = 4;
   if (const char* env = getenv("MW_RISBO_BLOCKS_PER_SM")) {
     const int v = atoi(env);
     if (v >= 1 && v <= 32) cap = v;

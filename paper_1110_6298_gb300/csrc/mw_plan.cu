@@ -66,7 +66,7 @@ cudaError_t upload_complex(const std::vector<double>& re, const std::vector<doub
 void free_plan(mw_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
-                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err, p->d_bar, p->d_rscale, p->d_nl, p->d_flmf};
+                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err, p->d_prog, p->d_rscale, p->d_nl, p->d_flmf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -222,7 +222,10 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
   alloc((void**)&p->d_err, sizeof(int));
   if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
-  alloc((void**)&p->d_bar, sizeof(unsigned));
+  {
+    const int Tm = (L + 1 + 31) / 32;
+    alloc((void**)&p->d_prog, sizeof(int) * (size_t)(Tm * (Tm + 1) / 2 + 1));
+  }
   if (e == cudaSuccess) {
     int nsm = 0;
     chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
