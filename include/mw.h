@@ -71,6 +71,12 @@ typedef enum {
  *                relative error below 1e-6 against the FP64 path. */
 enum { MW_PREC_FP64 = 0, MW_PREC_MIXED = 1 };
 
+/* MW_FLAG_GRAPH (or-ed into flags): the first call with a given (direction,
+ * input, output) captures the whole call into a CUDA graph, later calls with
+ * the same buffers replay it as one launch.  Not used while per-stage timing is
+ * on; if capture is not possible the plan runs its calls directly. */
+enum { MW_FLAG_GRAPH = 1 << 8 };
+
 /* Create a plan for `batch` maps of band limit L and spin s.
  * Requires 1 <= L <= 2048, |s| < L, batch >= 1, out != NULL.  Allocates the
  * device workspace on the current CUDA device; *out is NULL on failure. */
@@ -80,6 +86,17 @@ mw_status mw_plan_create(mw_plan **out, int L, int s, int batch, unsigned flags)
  * (|spins[b]| < L).  Maps of different spin share each Wigner-Delta plane,
  * which depends on neither L nor s (Sec. V footnote on multiple spins). */
 mw_status mw_plan_create_spins(mw_plan **out, int L, int batch, const int *spins, unsigned flags);
+
+/* Ragged batch: n maps, map b of band limit L[b] (1 <= L[b] <= 2048) and spin
+ * spins[b] (|spins[b]| < L[b]).  Buffers hold the maps (resp. f_lm blocks) back
+ * to back in the given order, each of its own size; mw_plan_map_elems and
+ * mw_plan_flm_elems give the totals.  One Wigner-Delta recursion to max L[b]
+ * serves every map (Delta^l depends on neither L nor s). */
+mw_status mw_plan_create_ragged(mw_plan **out, int n, const int *L, const int *spins, unsigned flags);
+
+/* Total complex elements of the plan's map buffer and f_lm buffer. */
+size_t mw_plan_map_elems(const mw_plan *plan);
+size_t mw_plan_flm_elems(const mw_plan *plan);
 
 /* Forward transform (Sec. IV-D): map_in [batch][N_MW] -> flm_out [batch][L*L].
  * The result is that of the paper's algorithm: phi DFT of each ring (Eq. Gmt

@@ -19,7 +19,7 @@ struct FftDesc {
 constexpr int kMaxGroupMaps = 32;
 constexpr int kChunk = 64;         // Delta planes staged per FP64 contraction launch
 constexpr int kTcChunk = 128;      // Delta planes staged per tensor-core contraction launch
-constexpr int kTcGroupMaps = 8;    // maps per spin group on the tensor-core path (N = 4 x 8)
+constexpr int kTcGroupMaps = 8;    // maps per spin group on both contraction paths (N = 4 x 8)
 
 struct SpinGroup {
   int s;
@@ -33,6 +33,14 @@ struct mw_plan {
   int prec = MW_PREC_FP64;
   int device = 0;
   std::vector<int> spins;          // per map
+  // caller-buffer offsets (complex elements) of each map and f_lm block
+  std::vector<long long> moff, foff;
+  long long* d_moff = nullptr;
+  long long* d_foff = nullptr;
+  long long map_elems = 0, flm_elems = 0;  // totals over the plan's maps
+  // ragged plans: one sub-plan per band limit; the parent owns the sweep state
+  std::vector<mw_plan*> subs;
+  bool shared_sweep = false;       // sweep state borrowed from a parent (not freed here)
   std::vector<SpinGroup> groups;   // host copy
   SpinGroup* d_groups = nullptr;   // device copy
   int* d_spins = nullptr;
@@ -67,6 +75,11 @@ struct mw_plan {
   size_t ws_bytes = 0;
   int last_launches = 0;
 
+  // CUDA graphs of whole calls (MW_FLAG_GRAPH): one per (direction, input, output)
+  struct GraphEntry { int dir; const void* in; void* out; cudaGraphExec_t exec; };
+  std::vector<GraphEntry> graphs;
+  bool graph_failed = false;       // capture unsupported here: run calls directly
+
   // optional per-stage timing (CUDA events on the call's stream)
   bool timing = false;
   struct Rec { int stage; cudaEvent_t a, b; };
@@ -98,11 +111,14 @@ cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStre
 cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st);
 cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const float2* flmf, cudaStream_t st);
 cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t st);
+cudaError_t launch_dmma_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st);
+cudaError_t launch_dmma_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st);
 cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st);
 
-// Wigner stage: sweep l = 0..L-1 with Risbo's recursion and contract.
+// Wigner stage: one sweep l = 0..o->L-1 with Risbo's recursion (state of the
+// owner o) and the contractions of the consumer plans cs[0..nc).
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
 int risbo_blocks_per_sm();
 
-cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out,
+cudaError_t run_wigner(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
                        cudaStream_t st, int* launches);

@@ -77,12 +77,13 @@ __device__ __forceinline__ int spin_of(const int* spins, int b) { return spins[b
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const double2* __restrict__ map,
+                              const long long* __restrict__ moff,
                               C<T>* __restrict__ Gt /* [B][M][L] */, const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int t = blockIdx.x, b = blockIdx.y;
   const int L = d.L, M = d.M;
-  const double2* f = map + (long long)b * d.nmw;
+  const double2* f = map + moff[b];
   C<T>* out = Gt + (long long)b * M * L;
   if (t == L - 1) {  // pole ring: 2 pi f(pi,0) delta_{m,s}
     const int s = spin_of(spins, b);
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDes
 
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ Gt,
-                              double2* __restrict__ map) {
+                              double2* __restrict__ map, const long long* __restrict__ moff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int L = d.L, M = d.M;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc 
   }
   __syncthreads();
   const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, true);
-  double2* f = map + (long long)b * d.nmw;
+  double2* f = map + moff[b];
   if (t < L - 1) {
     for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(res[p]);
   } else if (threadIdx.x == 0) {
@@ -306,13 +307,14 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d
 
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ Gt,
-                                      double2* __restrict__ map, const int* __restrict__ spins) {
+                                      double2* __restrict__ map, const long long* __restrict__ moff,
+                                      const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int L = d.L, M = d.M;
   const int t = blockIdx.x, b = blockIdx.y;
   const C<T>* in = Gt + ((long long)b * L + t) * M;
-  double2* f = map + (long long)b * d.nmw;
+  double2* f = map + moff[b];
   if (t == L - 1) {  // pole: sum_p e^{-i s phi_p} (2pi/M) sum_m e^{i m phi_p} G^H = 2 pi G^H_s
     if (threadIdx.x == 0) {
       const int s = spin_of(spins, b);
@@ -335,12 +337,13 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward_adjoint(Dims d, 
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse_adjoint(Dims d, FftDesc fM, const C<T>* __restrict__ twM,
-                                      const double2* __restrict__ map, C<T>* __restrict__ Gt /* [B][M][L] */) {
+                                      const double2* __restrict__ map, const long long* __restrict__ moff,
+                                      C<T>* __restrict__ Gt /* [B][M][L] */) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int L = d.L, M = d.M;
   const int t = blockIdx.x, b = blockIdx.y;
-  const double2* f = map + (long long)b * d.nmw;
+  const double2* f = map + moff[b];
   C<T>* out = Gt + (long long)b * M * L;
   if (t == L - 1) {  // only the phi = 0 sample of the pole ring is kept: F^H_m(pi) = x_pole
     const C<T> xp = from64<T>(f[(long long)(L - 1) * M]);
@@ -391,7 +394,8 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse_adjoint(Dims d
 // runs over m' >= 0 against u(m') + u(-m').  Evaluated this way the value does not
 // inherit the cancellation of the alternating sum over the FFT output.
 __global__ void k_pole_forward_adjoint(Dims d, const double2* __restrict__ Gp, const double2* __restrict__ upole,
-                                       double2* __restrict__ map, const int* __restrict__ spins) {
+                                       double2* __restrict__ map, const long long* __restrict__ moff,
+                                       const int* __restrict__ spins) {
   __shared__ double2 red[256];
   const int b = blockIdx.x, L = d.L, M = d.M;
   const int s = spin_of(spins, b);
@@ -416,7 +420,7 @@ __global__ void k_pole_forward_adjoint(Dims d, const double2* __restrict__ Gp, c
     if (s & 1) { ph.x = -ph.x; ph.y = -ph.y; }
     const double c = 2.0 * M_PI / M;
     const double2 v = red[0];
-    map[(long long)b * d.nmw + (long long)(L - 1) * M] =
+    map[moff[b] + (long long)(L - 1) * M] =
         make_double2(c * (ph.x * v.x - ph.y * v.y), c * (ph.x * v.y + ph.y * v.x));
   }
 }
@@ -456,7 +460,7 @@ cudaError_t phi_forward_t(const mw_plan* p, const double2* map, cudaStream_t st)
   cudaError_t e = set_smem(k_phi_forward<T>, sm);
   if (e != cudaSuccess) return e;
   k_phi_forward<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
-      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt, p->d_spins);
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, p->d_moff, (C<T>*)p->d_Gt, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
@@ -492,7 +496,7 @@ cudaError_t phi_inverse_t(const mw_plan* p, double2* map, cudaStream_t st) {
   cudaError_t e = set_smem(k_phi_inverse<T>, sm);
   if (e != cudaSuccess) return e;
   k_phi_inverse<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
-      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map);
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_moff);
   return cudaGetLastError();
 }
 template <typename T>
@@ -519,7 +523,7 @@ cudaError_t phi_forward_adjoint_t(const mw_plan* p, double2* map, cudaStream_t s
   cudaError_t e = set_smem(k_phi_forward_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
   k_phi_forward_adjoint<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
-      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_spins);
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_moff, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>
@@ -528,7 +532,7 @@ cudaError_t phi_inverse_adjoint_t(const mw_plan* p, const double2* map, cudaStre
   cudaError_t e = set_smem(k_phi_inverse_adjoint<T>, sm);
   if (e != cudaSuccess) return e;
   k_phi_inverse_adjoint<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
-      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, (C<T>*)p->d_Gt);
+      dims_of(p), p->fM, (const C<T>*)p->d_twM, map, p->d_moff, (C<T>*)p->d_Gt);
   return cudaGetLastError();
 }
 template <typename T>
@@ -567,6 +571,6 @@ cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st) {
   return DISPATCH(p, theta_inverse_adjoint_t, p, st);
 }
 cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st) {
-  k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_spins);
+  k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_moff, p->d_spins);
   return cudaGetLastError();
 }

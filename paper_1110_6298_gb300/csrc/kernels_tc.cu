@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
                                                          int l1, const SpinGroup* __restrict__ groups, int ng,
                                                          const float2* __restrict__ Gp,
                                                          const double* __restrict__ nltab,
-                                                         double2* __restrict__ flm, int* __restrict__ err) {
+                                                         double2* __restrict__ flm, const long long* __restrict__ foff,
+                                                         int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
   unsigned char* sB = smem + 3 * kATile;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
             default: o = make_double2(ai, -ar); break;
           }
         }
-        flm[(size_t)g.maps[neg ? j - nb : j] * L * L + (size_t)l * l + l + m] = o;
+        flm[foff[g.maps[neg ? j - nb : j]] + (size_t)l * l + l + m] = o;
       }
     }
   }
@@ -391,18 +392,20 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
 }  // namespace
 
 // N_l f_lm in FP32 for the inverse contraction (one block per (l, map)).
-__global__ void k_flm_to_f32(const double2* __restrict__ flm, float2* __restrict__ out, int L) {
+__global__ void k_flm_to_f32(const double2* __restrict__ flm, const long long* __restrict__ foff,
+                             float2* __restrict__ out, int L) {
   const int l = blockIdx.x, b = blockIdx.y;
   const float nl = sqrtf((2.f * l + 1.f) / (4.f * 3.14159265358979f));
   const size_t base = (size_t)b * L * L + (size_t)l * l;
+  const double2* src = flm + foff[b] + (size_t)l * l;
   for (int i = threadIdx.x; i < 2 * l + 1; i += blockDim.x) {
-    const double2 v = flm[base + i];
+    const double2 v = src[i];
     out[base + i] = make_float2((float)v.x * nl, (float)v.y * nl);
   }
 }
 
 cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t st) {
-  k_flm_to_f32<<<dim3(p->L, p->B), 128, 0, st>>>(flm, p->d_flmf, p->L);
+  k_flm_to_f32<<<dim3(p->L, p->B), 128, 0, st>>>(flm, p->d_foff, p->d_flmf, p->L);
   return cudaGetLastError();
 }
 
@@ -410,7 +413,7 @@ cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cu
   cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
   k_tc_forward<<<l1, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
-                                       reinterpret_cast<const float2*>(p->d_Gp), p->d_nl, flm, p->d_err);
+                                       reinterpret_cast<const float2*>(p->d_Gp), p->d_nl, flm, p->d_foff, p->d_err);
   return cudaGetLastError();
 }
 

@@ -18,10 +18,11 @@
 // Plane storage: quarter plane with rows a = mu - off and columns b = nu - off
 // (off = 0 for integer j, 1/2 for half-integer j), row stride LD = L + 1.
 //
-// The contraction uses the fold over +-m' (Delta_{-m',m} Delta_{-m',-s} =
-// (-1)^(m+s) Delta_{m'm} Delta_{m',-s}) so that it runs over m' >= 0 only, and
-// reads Delta_{m'm} from row |m| of the quarter plane through the transpose
-// symmetry, so every access is a contiguous row segment.
+// The contractions (kernels_tc.cu, kernels_dmma.cu) use the fold over +-m'
+// (Delta_{-m',m} Delta_{-m',-s} = (-1)^(m+s) Delta_{m'm} Delta_{m',-s}) so that
+// they run over m' >= 0 only, and read Delta_{m'm} from row |m| of the quarter
+// plane through the transpose symmetry, so every access is a contiguous row
+// segment.
 #include <cmath>
 #include <cstdlib>
 
@@ -268,145 +269,6 @@ __global__ void k_plane_init(double* S, float* S32) {
   if (S32) S32[0] = 1.0f;
 }
 
-// Forward contraction for planes l in [l0, l1) stored at slots l % kChunk:
-//   f_lm = (-1)^s i^(m+s) N_l sum_{m'=0}^{l} K_m[l,m'] G+_{m,m'},
-//   K_m[l,m'] = Delta^l_{m'm} Delta^l_{m',-s}.
-// One block per (m, spin group); rows l of the chunk x maps of the group.
-constexpr int kTileMp = 64;
-
-__global__ void k_contract_forward(const double* __restrict__ S, int LD, int L, int M, int l0, int l1,
-                                   const SpinGroup* __restrict__ groups, const double2* __restrict__ Gp,
-                                   double2* __restrict__ flm, const double* __restrict__ nltab) {
-  __shared__ double Kt[kChunk][kTileMp + 1];
-  __shared__ double2 Gs[kMaxGroupMaps][kTileMp];
-  const int im = blockIdx.x, m = im - (L - 1), am = m < 0 ? -m : m;
-  const SpinGroup& g = groups[blockIdx.y];
-  const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
-  const int lstart = max(l0, am);
-  if (lstart >= l1) return;
-  const int nl = l1 - l0;
-  const int npairs = nl * nb;
-  // per-thread accumulators over (l, map) pairs
-  constexpr int kMaxPairsPerThread = (kChunk * kMaxGroupMaps + 255) / 256;
-  double ar[kMaxPairsPerThread], ai[kMaxPairsPerThread];
-#pragma unroll
-  for (int q = 0; q < kMaxPairsPerThread; ++q) { ar[q] = 0.0; ai[q] = 0.0; }
-  const int lmax = l1 - 1;
-  for (int mp0 = 0; mp0 <= lmax; mp0 += kTileMp) {
-    // K tile: rows l (chunk), columns m' in [mp0, mp0 + kTileMp)
-    for (int idx = threadIdx.x; idx < nl * kTileMp; idx += blockDim.x) {
-      const int r = idx / kTileMp, c = idx % kTileMp;
-      const int l = l0 + r, mp = mp0 + c;
-      double k = 0.0;
-      if (l >= lstart && l >= as && mp <= l) {
-        const double* P = S + (size_t)(l % kChunk) * LD * LD;
-        // Delta_{m'|m|} = (-1)^(m'-|m|) P[|m|][m'], Delta_{m'|s|} likewise
-        double v = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
-        int ex = am + as;                      // (-1)^(m'-|m|) (-1)^(m'-|s|)
-        if (m < 0) ex += l + mp;               // Delta_{m',-|m|} = (-1)^(l+m') Delta_{m',|m|}
-        if (s > 0) ex += l + mp;               // Delta_{m',-s} for s > 0
-        k = sgn_pow(ex) * v;
-      }
-      Kt[r][c] = k;
-    }
-    for (int idx = threadIdx.x; idx < nb * kTileMp; idx += blockDim.x) {
-      const int bb = idx / kTileMp, c = idx % kTileMp;
-      const int mp = mp0 + c;
-      Gs[bb][c] = (mp < L) ? Gp[((size_t)g.maps[bb] * M + im) * L + mp] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kMaxPairsPerThread; ++q) {
-      const int pidx = threadIdx.x + q * blockDim.x;
-      if (pidx < npairs) {
-        const int r = pidx / nb, bb = pidx % nb;
-        double sr = ar[q], si = ai[q];
-        for (int c = 0; c < kTileMp; ++c) {
-          const double k = Kt[r][c];
-          const double2 gv = Gs[bb][c];
-          sr = fma(k, gv.x, sr);
-          si = fma(k, gv.y, si);
-        }
-        ar[q] = sr; ai[q] = si;
-      }
-    }
-    __syncthreads();
-  }
-  // epilogue: times (-1)^s i^(m+s) N_l, write f_lm (zero for l < |s|)
-  const int r4 = (m + s) & 3;
-  const double pr = (r4 == 0) ? 1.0 : (r4 == 2 ? -1.0 : 0.0);
-  const double pi_ = (r4 == 1) ? 1.0 : (r4 == 3 ? -1.0 : 0.0);
-  const double sgs = sgn_pow(s);
-#pragma unroll
-  for (int q = 0; q < kMaxPairsPerThread; ++q) {
-    const int pidx = threadIdx.x + q * blockDim.x;
-    if (pidx < npairs) {
-      const int r = pidx / nb, bb = pidx % nb;
-      const int l = l0 + r;
-      if (l < lstart) continue;
-      double2 o = make_double2(0.0, 0.0);
-      if (l >= as) {
-        const double nl_ = sgs * nltab[l];
-        o.x = nl_ * (pr * ar[q] - pi_ * ai[q]);
-        o.y = nl_ * (pr * ai[q] + pi_ * ar[q]);
-      }
-      flm[(size_t)g.maps[bb] * L * L + (size_t)l * l + l + m] = o;
-    }
-  }
-}
-
-// Inverse contraction, accumulated over chunks into F+ (m' >= 0):
-//   F+_{m,m'} += sum_{l in chunk} N_l K_m[l,m'] f_lm
-// (the phase (-1)^s i^-(m+s) is applied when F is unfolded).
-// One block per (m, m'-tile, spin group).
-__global__ void k_contract_inverse(const double* __restrict__ S, int LD, int L, int M, int l0, int l1,
-                                   const SpinGroup* __restrict__ groups, const double2* __restrict__ flm,
-                                   double2* __restrict__ Fp, const double* __restrict__ nltab) {
-  __shared__ double Kt[kChunk][kTileMp + 1];
-  __shared__ double2 Fs[kMaxGroupMaps][kChunk];
-  const int im = blockIdx.x, m = im - (L - 1), am = m < 0 ? -m : m;
-  const int mp0 = blockIdx.y * kTileMp;
-  const SpinGroup& g = groups[blockIdx.z];
-  const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
-  const int lstart = max(max(l0, am), as);
-  if (lstart >= l1 || mp0 > l1 - 1) return;
-  const int nl = l1 - l0;
-  for (int idx = threadIdx.x; idx < nl * kTileMp; idx += blockDim.x) {
-    const int r = idx / kTileMp, c = idx % kTileMp;
-    const int l = l0 + r, mp = mp0 + c;
-    double k = 0.0;
-    if (l >= lstart && mp <= l) {
-      const double* P = S + (size_t)(l % kChunk) * LD * LD;
-      double v = P[(size_t)am * LD + mp] * P[(size_t)as * LD + mp];
-      int ex = am + as;
-      if (m < 0) ex += l + mp;
-      if (s > 0) ex += l + mp;
-      k = sgn_pow(ex) * v * nltab[l];
-    }
-    Kt[r][c] = k;
-  }
-  for (int idx = threadIdx.x; idx < nb * nl; idx += blockDim.x) {
-    const int bb = idx / nl, r = idx % nl;
-    const int l = l0 + r;
-    Fs[bb][r] = (l >= lstart) ? flm[(size_t)g.maps[bb] * L * L + (size_t)l * l + l + m] : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
-  for (int pidx = threadIdx.x; pidx < kTileMp * nb; pidx += blockDim.x) {
-    const int c = pidx % kTileMp, bb = pidx / kTileMp;
-    const int mp = mp0 + c;
-    if (mp >= L) continue;
-    double2* dst = Fp + ((size_t)g.maps[bb] * M + im) * L + mp;
-    double sr = dst->x, si = dst->y;
-    for (int r = 0; r < nl; ++r) {
-      const double k = Kt[r][c];
-      const double2 f = Fs[bb][r];
-      sr = fma(k, f.x, sr);
-      si = fma(k, f.y, si);
-    }
-    *dst = make_double2(sr, si);
-  }
-}
-
 }  // namespace
 
 namespace {
@@ -427,72 +289,51 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
   return e;
 }
 
-cudaError_t run_wigner_fp64(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
-                            int* launches) {
-  const int L = p->L, M = p->M, LD = p->LD;
-  const int ng = (int)p->groups.size();
+// One Risbo sweep (recursion state and staging of the owner o) feeding the
+// contractions of the consumer plans cs (for a regular plan o == cs[0]; for a
+// ragged plan the consumers are the per-band-limit sub-plans).  Plane l serves
+// every consumer with L > l: Delta^l depends on neither L nor s.
+cudaError_t run_sweep(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
+                      cudaStream_t st, int* launches) {
+  const bool fp64 = o->prec == MW_PREC_FP64;
+  const int chunk = fp64 ? kChunk : kTcChunk;
   int nl = 0;
   cudaError_t e;
   if (mode == 1) {
-    e = cudaMemsetAsync(p->d_Gp, 0, sizeof(double2) * (size_t)p->B * M * L, st);
-    if (e != cudaSuccess) return e;
-  }
-  k_plane_init<<<1, 1, 0, st>>>(p->d_S, nullptr);
-  ++nl;
-  for (int l0 = 0; l0 < L; l0 += kChunk) {
-    const int l1 = (l0 + kChunk < L) ? l0 + kChunk : L;
-    StageSpan span_d(p, MW_STAGE_DELTA, st);
-    int nd = 0;
-    e = launch_risbo(p, p->d_S, kChunk, nullptr, l0, 1, (l0 == 0 ? 1 : l0), l1, st, &nd);
-    if (e != cudaSuccess) return e;
-    span_d.end(nd);
-    nl += nd;
-    StageSpan span_c(p, MW_STAGE_CONTRACT, st);
-    if (mode == 0) {
-      k_contract_forward<<<dim3(M, ng), 256, 0, st>>>(p->d_S, LD, L, M, l0, l1, p->d_groups, p->d_Gp, flm_out,
-                                                      p->d_nl);
-    } else {
-      k_contract_inverse<<<dim3(M, (l1 + kTileMp - 1) / kTileMp, ng), 256, 0, st>>>(
-          p->d_S, LD, L, M, l0, l1, p->d_groups, flm_in, p->d_Gp, p->d_nl);
+    for (int c = 0; c < nc; ++c) {
+      e = cudaMemsetAsync(cs[c]->d_Gp, 0, sizeof(double2) * (size_t)cs[c]->B * cs[c]->M * cs[c]->L, st);
+      if (e != cudaSuccess) return e;
+      if (!fp64) {
+        e = launch_flm_to_f32(cs[c], flm_in, st);
+        if (e != cudaSuccess) return e;
+        ++nl;
+      }
     }
-    span_c.end(1);
-    ++nl;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
-  if (launches) *launches += nl;
-  return cudaGetLastError();
-}
-
-// Mixed path: FP64 recursion state in two ping-pong planes, FP32 copies of the
-// integer planes of a 128-plane chunk for the tensor-core contraction.
-cudaError_t run_wigner_mixed(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
-                             int* launches) {
-  const int L = p->L, M = p->M;
-  int nl = 0;
-  cudaError_t e;
-  if (mode == 1) {
-    e = cudaMemsetAsync(p->d_Gp, 0, sizeof(double2) * (size_t)p->B * M * L, st);
-    if (e != cudaSuccess) return e;
-    e = launch_flm_to_f32(p, flm_in, st);
-    if (e != cudaSuccess) return e;
-    ++nl;
-  }
-  k_plane_init<<<1, 1, 0, st>>>(p->d_S, p->d_S32);
+  k_plane_init<<<1, 1, 0, st>>>(o->d_S, fp64 ? nullptr : o->d_S32);
   ++nl;
-  for (int l0 = 0; l0 < L; l0 += kTcChunk) {
-    const int l1 = (l0 + kTcChunk < L) ? l0 + kTcChunk : L;
-    StageSpan span_d(p, MW_STAGE_DELTA, st);
+  for (int l0 = 0; l0 < o->L; l0 += chunk) {
+    const int l1 = (l0 + chunk < o->L) ? l0 + chunk : o->L;
+    StageSpan span_d(o, MW_STAGE_DELTA, st);
     int nd = 0;
-    e = launch_risbo(p, p->d_S, 2, p->d_S32, l0, 0, (l0 == 0 ? 1 : l0), l1, st, &nd);
+    e = launch_risbo(o, o->d_S, fp64 ? kChunk : 2, fp64 ? nullptr : o->d_S32, l0, fp64 ? 1 : 0, (l0 == 0 ? 1 : l0),
+                     l1, st, &nd);
     if (e != cudaSuccess) return e;
     span_d.end(nd);
     nl += nd;
-    StageSpan span_c(p, MW_STAGE_CONTRACT, st);
-    e = (mode == 0) ? launch_tc_forward(p, l0, l1, flm_out, st) : launch_tc_inverse(p, l0, l1, p->d_flmf, st);
-    span_c.end(1);
-    ++nl;
-    if (e != cudaSuccess) return e;
+    StageSpan span_c(o, MW_STAGE_CONTRACT, st);
+    int ncl = 0;
+    for (int c = 0; c < nc; ++c) {
+      mw_plan* q = cs[c];
+      if (q->L <= l0) continue;
+      const int l1c = l1 < q->L ? l1 : q->L;
+      if (fp64) e = (mode == 0) ? launch_dmma_forward(q, l0, l1c, flm_out, st) : launch_dmma_inverse(q, l0, l1c, flm_in, st);
+      else e = (mode == 0) ? launch_tc_forward(q, l0, l1c, flm_out, st) : launch_tc_inverse(q, l0, l1c, q->d_flmf, st);
+      ++ncl;
+      if (e != cudaSuccess) return e;
+    }
+    span_c.end(ncl);
+    nl += ncl;
   }
   if (launches) *launches += nl;
   return cudaGetLastError();
@@ -516,8 +357,7 @@ int risbo_blocks_per_sm() {
   return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
-cudaError_t run_wigner(mw_plan* p, int mode, const double2* flm_in, double2* flm_out, cudaStream_t st,
-                       int* launches) {
-  return p->prec == MW_PREC_FP64 ? run_wigner_fp64(p, mode, flm_in, flm_out, st, launches)
-                                 : run_wigner_mixed(p, mode, flm_in, flm_out, st, launches);
+cudaError_t run_wigner(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
+                       cudaStream_t st, int* launches) {
+  return run_sweep(o, cs, nc, mode, flm_in, flm_out, st, launches);
 }

@@ -65,10 +65,14 @@ cudaError_t upload_complex(const std::vector<double>& re, const std::vector<doub
 
 void free_plan(mw_plan* p) {
   if (!p) return;
+  for (mw_plan* c : p->subs) free_plan(c);
+  if (p->shared_sweep) { p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; }
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
-                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err, p->d_prog, p->d_rscale, p->d_nl, p->d_flmf};
+                  p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
+                  p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto ev : p->pool) cudaEventDestroy(ev);
   delete p;
@@ -80,12 +84,18 @@ mw_status from_cuda(cudaError_t e) {
   return MW_ECUDA;
 }
 
-mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned flags) {
+// Build a plan for B maps of band limit L.  moff / foff: caller-buffer offsets of
+// each map / f_lm block (NULL: contiguous).  owner: a ragged parent whose sweep
+// state (planes, staging, progress and error words) this plan borrows; its row
+// stride LD is used.  sweep_only: allocate only the sweep state (ragged parent).
+mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned flags, const long long* moff = nullptr,
+                     const long long* foff = nullptr, mw_plan* owner = nullptr, bool sweep_only = false) {
   if (!out) return MW_EINVAL;
   *out = nullptr;
   if (L < 1 || L > 2048 || B < 1 || !spins) return MW_EINVAL;
   const int prec = (int)(flags & 0xffu);
   if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED) return MW_EINVAL;
+  if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH)) return MW_EINVAL;
   for (int b = 0; b < B; ++b)
     if (spins[b] <= -L || spins[b] >= L) return MW_EINVAL;
 
@@ -99,14 +109,23 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   p->N = N;
   p->flags = flags;
   p->prec = prec;
-  p->LD = ((L + 1 + 7) / 8) * 8;  // 32-byte aligned plane rows
+  p->LD = owner ? owner->LD : ((L + 1 + 7) / 8) * 8;  // 32-byte aligned plane rows
   cudaGetDevice(&p->device);
   p->spins.assign(spins, spins + B);
+  const long long nmw = (long long)(L - 1) * (2 * L - 1) + 1;
+  p->moff.resize(B);
+  p->foff.resize(B);
+  for (int b = 0; b < B; ++b) {
+    p->moff[b] = moff ? moff[b] : (long long)b * nmw;
+    p->foff[b] = foff ? foff[b] : (long long)b * L * L;
+  }
+  p->map_elems = (long long)B * nmw;
+  p->flm_elems = (long long)B * L * L;
   if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
 
   // spin groups (order of first appearance; at most kMaxGroupMaps maps each,
   // kTcGroupMaps on the tensor-core path)
-  const int gmax = prec == MW_PREC_MIXED ? kTcGroupMaps : kMaxGroupMaps;
+  const int gmax = kTcGroupMaps;
   for (int b = 0; b < B; ++b) {
     SpinGroup* g = nullptr;
     for (auto& h : p->groups)
@@ -138,6 +157,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     for (int k = 0; k < n; ++k) unit_root(k, n, &re[k], &im[k]);
   };
   const bool dbl = prec == MW_PREC_FP64;
+  if (!sweep_only) {
   twiddles(M);
   chk(dbl ? upload_complex<double>(re, im, &p->d_twM) : upload_complex<float>(re, im, &p->d_twM));
   twiddles(N);
@@ -167,13 +187,14 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     }
     chk(dbl ? upload_complex<double>(re, im, &p->d_V) : upload_complex<float>(re, im, &p->d_V));
   }
+  }  // !sweep_only
   {
     std::vector<double> sq(2 * L + 3);
     for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
     alloc((void**)&p->d_sqrt, sizeof(double) * sq.size());
     if (e == cudaSuccess) chk(cudaMemcpy(p->d_sqrt, sq.data(), sizeof(double) * sq.size(), cudaMemcpyHostToDevice));
   }
-  {  // u(m') = sum_{|m''| <= L-1} (-1)^{m''} conj(w(m''-m')); folded u(m') + u(-m') for m' > 0
+  if (!sweep_only) {  // u(m') = sum_{|m''| <= L-1} (-1)^{m''} conj(w(m''-m')); folded u(m') + u(-m') for m' > 0
     auto u = [&](int mp, double* ur, double* ui) {
       double sr = 0.0, si = 0.0;
       for (int mpp = -(L - 1); mpp <= L - 1; ++mpp) {
@@ -207,29 +228,43 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   }
   alloc((void**)&p->d_spins, sizeof(int) * B);
   if (e == cudaSuccess) chk(cudaMemcpy(p->d_spins, spins, sizeof(int) * B, cudaMemcpyHostToDevice));
+  alloc((void**)&p->d_moff, sizeof(long long) * B);
+  if (e == cudaSuccess) chk(cudaMemcpy(p->d_moff, p->moff.data(), sizeof(long long) * B, cudaMemcpyHostToDevice));
+  alloc((void**)&p->d_foff, sizeof(long long) * B);
+  if (e == cudaSuccess) chk(cudaMemcpy(p->d_foff, p->foff.data(), sizeof(long long) * B, cudaMemcpyHostToDevice));
   alloc((void**)&p->d_groups, sizeof(SpinGroup) * p->groups.size());
   if (e == cudaSuccess)
     chk(cudaMemcpy(p->d_groups, p->groups.data(), sizeof(SpinGroup) * p->groups.size(), cudaMemcpyHostToDevice));
 
   // workspace
   const size_t fsz = dbl ? sizeof(double2) : sizeof(float2);
-  alloc(&p->d_Gt, fsz * (size_t)B * M * L);
-  alloc((void**)&p->d_Gp, sizeof(double2) * (size_t)B * M * L);
-  const size_t plane = (size_t)p->LD * p->LD;
-  alloc((void**)&p->d_S, sizeof(double) * (dbl ? (size_t)kChunk : 2) * plane);
-  alloc((void**)&p->d_H, sizeof(double) * plane);
-  if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)kTcChunk * plane);
-  if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
-  alloc((void**)&p->d_err, sizeof(int));
-  if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
-  {
-    const int Tm = (L + 1 + 31) / 32;
-    alloc((void**)&p->d_prog, sizeof(int) * (size_t)(Tm * (Tm + 1) / 2 + 1));
+  if (!sweep_only) {
+    alloc(&p->d_Gt, fsz * (size_t)B * M * L);
+    alloc((void**)&p->d_Gp, sizeof(double2) * (size_t)B * M * L);
+    if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
   }
-  if (e == cudaSuccess) {
-    int nsm = 0;
-    chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-    p->risbo_grid = nsm * risbo_blocks_per_sm();
+  if (owner) {  // borrow the parent's sweep state
+    p->shared_sweep = true;
+    p->d_S = owner->d_S;
+    p->d_S32 = owner->d_S32;
+    p->d_err = owner->d_err;
+    p->d_prog = owner->d_prog;
+    p->risbo_grid = owner->risbo_grid;
+  } else {
+    const size_t plane = (size_t)p->LD * p->LD;
+    alloc((void**)&p->d_S, sizeof(double) * (dbl ? (size_t)kChunk : 2) * plane);
+    if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)kTcChunk * plane);
+    alloc((void**)&p->d_err, sizeof(int));
+    if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
+    {
+      const int Tm = (L + 1 + 31) / 32;
+      alloc((void**)&p->d_prog, sizeof(int) * (size_t)(Tm * (Tm + 1) / 2 + 1));
+    }
+    if (e == cudaSuccess) {
+      int nsm = 0;
+      chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+      p->risbo_grid = nsm * risbo_blocks_per_sm();
+    }
   }
   if (e != cudaSuccess) {
     const mw_status st = from_cuda(e);
@@ -256,20 +291,24 @@ enum Direction { kForward, kInverse, kForwardAdjoint, kInverseAdjoint };
 mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream) {
   if (!p || !in || !out) return MW_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t nmw = (size_t)(p->L - 1) * p->M + 1, nlm = (size_t)p->L * p->L;
+  // consumers: the plan itself, or the per-band-limit sub-plans of a ragged plan
+  std::vector<mw_plan*> cs;
+  if (p->subs.empty()) cs.push_back(p);
+  else cs = p->subs;
+  const size_t nmw = (size_t)p->map_elems, nlm = (size_t)p->flm_elems;
   const bool map_in = (dir == kForward || dir == kInverseAdjoint);
-  const size_t in_elems = (map_in ? nmw : nlm) * p->B, out_elems = (map_in ? nlm : nmw) * p->B;
+  const size_t in_elems = map_in ? nmw : nlm, out_elems = map_in ? nlm : nmw;
   const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
   cudaError_t e = cudaSuccess;
   // host staging buffers are allocated on first use
   if (!in_dev || !out_dev) {
     if (!p->d_map_stage) {
-      e = cudaMalloc((void**)&p->d_map_stage, sizeof(double2) * nmw * p->B);
-      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nmw * p->B;
+      e = cudaMalloc((void**)&p->d_map_stage, sizeof(double2) * nmw);
+      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nmw;
     }
     if (e == cudaSuccess && !p->d_flm_stage) {
-      e = cudaMalloc((void**)&p->d_flm_stage, sizeof(double2) * nlm * p->B);
-      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nlm * p->B;
+      e = cudaMalloc((void**)&p->d_flm_stage, sizeof(double2) * nlm);
+      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nlm;
     }
     if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
   }
@@ -284,33 +323,39 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   if (!out_dev) dout = map_in ? p->d_flm_stage : p->d_map_stage;
 
   int nl = 0;
+  auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+  // one FFT stage for every consumer, timed as one span on the plan
   auto stage = [&](int stg, cudaError_t (*fn)(const mw_plan*, cudaStream_t)) {
     if (e != cudaSuccess) return;
     StageSpan sp(p, stg, st);
-    e = fn(p, st);
-    sp.end(1);
-    ++nl;
+    for (mw_plan* c : cs) {
+      if (e == cudaSuccess) e = fn(c, st);
+      ++nl;
+    }
+    sp.end((int)cs.size());
   };
   auto phi = [&](auto fn, auto ptr) {
     if (e != cudaSuccess) return;
     StageSpan sp(p, MW_STAGE_PHI, st);
-    e = fn(p, ptr, st);
-    sp.end(1);
-    ++nl;
+    for (mw_plan* c : cs) {
+      if (e == cudaSuccess) e = fn(c, ptr, st);
+      ++nl;
+    }
+    sp.end((int)cs.size());
   };
   switch (dir) {
     case kForward:
       phi(launch_phi_forward, din);
       stage(MW_STAGE_THETA, launch_theta_forward);
-      if (e == cudaSuccess) e = run_wigner(p, 0, nullptr, dout, st, &nl);
+      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 0, nullptr, dout, st, &nl);
       break;
     case kInverse:
-      if (e == cudaSuccess) e = run_wigner(p, 1, din, nullptr, st, &nl);
+      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 1, din, nullptr, st, &nl);
       stage(MW_STAGE_THETA, launch_theta_inverse);
       phi(launch_phi_inverse, dout);
       break;
     case kForwardAdjoint:
-      if (e == cudaSuccess) e = run_wigner(p, 1, din, nullptr, st, &nl);
+      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 1, din, nullptr, st, &nl);
       stage(MW_STAGE_THETA, launch_theta_forward_adjoint);
       phi(launch_phi_forward_adjoint, dout);
       phi(launch_pole_forward_adjoint, dout);
@@ -318,16 +363,113 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
     case kInverseAdjoint:
       phi(launch_phi_inverse_adjoint, din);
       stage(MW_STAGE_THETA, launch_theta_inverse_adjoint);
-      if (e == cudaSuccess) e = run_wigner(p, 0, nullptr, dout, st, &nl);
+      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 0, nullptr, dout, st, &nl);
       break;
   }
-  p->last_launches = nl;
+  return e;
+  };
+  // CUDA graph: captured on the first call with these buffers, replayed after
+  bool ran = false;
+  if ((p->flags & MW_FLAG_GRAPH) && !p->timing && !p->graph_failed) {
+    for (auto& g : p->graphs)
+      if (g.dir == (int)dir && g.in == (const void*)din && g.out == (void*)dout) {
+        e = cudaGraphLaunch(g.exec, st);
+        p->last_launches = 1;
+        ran = true;
+        break;
+      }
+    if (!ran) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        cudaError_t ee = enqueue(st);
+        ce = cudaStreamEndCapture(st, &graph);
+        if (ee != cudaSuccess) ce = ee;
+      }
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ce == cudaSuccess) {
+        if (p->graphs.size() >= 8) {
+          cudaGraphExecDestroy(p->graphs.front().exec);
+          p->graphs.erase(p->graphs.begin());
+        }
+        p->graphs.push_back({(int)dir, (const void*)din, (void*)dout, exec});
+        e = cudaGraphLaunch(exec, st);
+        p->last_launches = 1;
+        ran = true;
+      } else {
+        cudaGetLastError();  // capture not possible here: fall back to direct launches
+        p->graph_failed = true;
+        e = cudaSuccess;
+        nl = 0;
+      }
+    }
+  }
+  if (!ran) {
+    e = enqueue(st);
+    p->last_launches = nl;
+  }
   if (e != cudaSuccess) return from_cuda(e);
   if (!out_dev) {
     e = cudaMemcpyAsync(out, dout, sizeof(double2) * out_elems, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
   }
+  return MW_OK;
+}
+
+// Ragged plan: n maps with their own band limits and spins.  The parent owns
+// the recursion state sized for max L; one sub-plan per distinct band limit
+// owns that band limit's tables and buffers and reads/writes its maps at their
+// offsets in the caller's buffers (maps and f_lm blocks back to back in the
+// caller's order).
+mw_status build_ragged(mw_plan** out, int n, const int* Ls, const int* spins, unsigned flags) {
+  if (!out) return MW_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > (1 << 20) || !Ls || !spins) return MW_EINVAL;
+  int Lmax = 0;
+  std::vector<long long> moff(n), foff(n);
+  long long mo = 0, fo = 0;
+  for (int b = 0; b < n; ++b) {
+    if (Ls[b] < 1 || Ls[b] > 2048 || spins[b] <= -Ls[b] || spins[b] >= Ls[b]) return MW_EINVAL;
+    Lmax = Ls[b] > Lmax ? Ls[b] : Lmax;
+    moff[b] = mo;
+    foff[b] = fo;
+    mo += (long long)(Ls[b] - 1) * (2 * Ls[b] - 1) + 1;
+    fo += (long long)Ls[b] * Ls[b];
+  }
+  const int zero = 0;
+  mw_plan* parent = nullptr;
+  mw_status stt = build_plan(&parent, Lmax, 1, &zero, flags, nullptr, nullptr, nullptr, true);
+  if (stt != MW_OK) return stt;
+  parent->B = n;
+  parent->spins.assign(spins, spins + n);
+  parent->map_elems = mo;
+  parent->flm_elems = fo;
+  std::vector<int> done(n, 0);
+  for (int b = 0; b < n; ++b) {
+    if (done[b]) continue;
+    const int L = Ls[b];
+    std::vector<int> ss;
+    std::vector<long long> mm, ff;
+    for (int c = b; c < n; ++c)
+      if (!done[c] && Ls[c] == L) {
+        done[c] = 1;
+        ss.push_back(spins[c]);
+        mm.push_back(moff[c]);
+        ff.push_back(foff[c]);
+      }
+    mw_plan* sub = nullptr;
+    stt = build_plan(&sub, L, (int)ss.size(), ss.data(), flags, mm.data(), ff.data(), parent, false);
+    if (stt != MW_OK) {
+      free_plan(parent);
+      return stt;
+    }
+    parent->ws_bytes += sub->ws_bytes;
+    parent->subs.push_back(sub);
+  }
+  *out = parent;
   return MW_OK;
 }
 
@@ -409,6 +551,10 @@ mw_status mw_plan_create(mw_plan** out, int L, int s, int batch, unsigned flags)
   return build_plan(out, L, batch, spins.data(), flags);
 }
 
+mw_status mw_plan_create_ragged(mw_plan** out, int n, const int* L, const int* spins, unsigned flags) {
+  return build_ragged(out, n, L, spins, flags);
+}
+
 mw_status mw_plan_create_spins(mw_plan** out, int L, int batch, const int* spins, unsigned flags) {
   if (!out) return MW_EINVAL;
   *out = nullptr;
@@ -447,6 +593,9 @@ const char* mw_status_string(mw_status st) {
   }
   return "unknown status";
 }
+
+size_t mw_plan_map_elems(const mw_plan* plan) { return plan ? (size_t)plan->map_elems : 0; }
+size_t mw_plan_flm_elems(const mw_plan* plan) { return plan ? (size_t)plan->flm_elems : 0; }
 
 size_t mw_map_size(int L) { return L < 1 ? 0 : (size_t)(L - 1) * (2 * (size_t)L - 1) + 1; }
 size_t mw_flm_size(int L) { return L < 1 ? 0 : (size_t)L * (size_t)L; }

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ENOMEM, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = range(6)
 PRECISIONS = {"fp64": 0, "mixed": 1}
+FLAG_GRAPH = 1 << 8
 
 _lib = None
 
@@ -36,6 +37,13 @@ def lib():
         vp, c_int, c_uint, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
         L.mw_plan_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, c_uint]
         L.mw_plan_create_spins.argtypes = [ctypes.POINTER(vp), c_int, c_int, ctypes.POINTER(c_int), c_uint]
+        L.mw_plan_create_ragged.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                            c_uint]
+        L.mw_plan_create_ragged.restype = c_int
+        L.mw_plan_map_elems.argtypes = [vp]
+        L.mw_plan_map_elems.restype = c_size
+        L.mw_plan_flm_elems.argtypes = [vp]
+        L.mw_plan_flm_elems.restype = c_size
         for name in ("mw_forward", "mw_inverse", "mw_forward_adjoint", "mw_inverse_adjoint"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
             getattr(L, name).restype = c_int
@@ -85,7 +93,7 @@ def _stream_of(t):
 class Plan:
     """A transform plan: L, one spin per map (or one spin for all), precision."""
 
-    def __init__(self, L, spins, batch=None, precision="fp64"):
+    def __init__(self, L, spins, batch=None, precision="fp64", graph=False):
         if isinstance(spins, int):
             if batch is None:
                 batch = 1
@@ -97,10 +105,13 @@ class Plan:
         self.precision = precision
         h = ctypes.c_void_p()
         arr = (ctypes.c_int * len(spins))(*spins)
-        st = lib().mw_plan_create_spins(ctypes.byref(h), self.L, self.batch, arr, PRECISIONS[precision])
+        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0)
+        st = lib().mw_plan_create_spins(ctypes.byref(h), self.L, self.batch, arr, flags)
         if st != MW_OK:
             raise MWError(st, "mw_plan_create_spins")
         self._h = h
+        self._nmap = self.batch * map_size(self.L)
+        self._nflm = self.batch * flm_size(self.L)
 
     @property
     def handle(self):
@@ -152,12 +163,13 @@ class Plan:
     def _call(self, name, x, n_in, n_out, out):
         if x.dtype != torch.complex128:
             raise TypeError("expected a complex128 tensor")
-        if x.numel() != self.batch * n_in:
-            raise ValueError(f"expected {self.batch}x{n_in} elements, got {tuple(x.shape)}")
+        if x.numel() != n_in:
+            raise ValueError(f"expected {n_in} elements, got {tuple(x.shape)}")
         x = x.contiguous()
         if out is None:
-            out = torch.empty((self.batch, n_out), dtype=torch.complex128, device=x.device)
-        elif out.dtype != torch.complex128 or out.numel() != self.batch * n_out or not out.is_contiguous():
+            shape = (self.batch, n_out // self.batch) if n_out % self.batch == 0 and self._uniform else (n_out,)
+            out = torch.empty(shape, dtype=torch.complex128, device=x.device)
+        elif out.dtype != torch.complex128 or out.numel() != n_out or not out.is_contiguous():
             raise ValueError("bad output tensor")
         st = getattr(lib(), name)(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                   _stream_of(x))
@@ -165,14 +177,50 @@ class Plan:
             raise MWError(st, name)
         return out
 
+    _uniform = True
+
     def forward(self, maps, out=None):
-        return self._call("mw_forward", maps, map_size(self.L), flm_size(self.L), out)
+        return self._call("mw_forward", maps, self._nmap, self._nflm, out)
 
     def inverse(self, flm, out=None):
-        return self._call("mw_inverse", flm, flm_size(self.L), map_size(self.L), out)
+        return self._call("mw_inverse", flm, self._nflm, self._nmap, out)
 
     def forward_adjoint(self, flm, out=None):
-        return self._call("mw_forward_adjoint", flm, flm_size(self.L), map_size(self.L), out)
+        return self._call("mw_forward_adjoint", flm, self._nflm, self._nmap, out)
 
     def inverse_adjoint(self, maps, out=None):
-        return self._call("mw_inverse_adjoint", maps, map_size(self.L), flm_size(self.L), out)
+        return self._call("mw_inverse_adjoint", maps, self._nmap, self._nflm, out)
+
+
+class RaggedPlan(Plan):
+    """n maps of their own band limits Ls[b] and spins spins[b] in one plan.
+
+    Buffers are flat: the maps (resp. f_lm blocks) back to back in the given
+    order; map_offsets / flm_offsets give where each starts."""
+
+    _uniform = False
+
+    def __init__(self, Ls, spins, precision="mixed", graph=False):
+        Ls = [int(x) for x in Ls]
+        spins = [int(x) for x in spins]
+        if len(Ls) != len(spins):
+            raise ValueError("Ls and spins differ in length")
+        self.Ls, self.spins, self.batch, self.L = Ls, spins, len(Ls), max(Ls)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        la = (ctypes.c_int * len(Ls))(*Ls)
+        sa = (ctypes.c_int * len(spins))(*spins)
+        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0)
+        st = lib().mw_plan_create_ragged(ctypes.byref(h), len(Ls), la, sa, flags)
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_create_ragged")
+        self._h = h
+        self._nmap = int(lib().mw_plan_map_elems(h))
+        self._nflm = int(lib().mw_plan_flm_elems(h))
+        self.map_offsets, self.flm_offsets = [], []
+        mo = fo = 0
+        for L in Ls:
+            self.map_offsets.append(mo)
+            self.flm_offsets.append(fo)
+            mo += map_size(L)
+            fo += flm_size(L)
