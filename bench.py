@@ -94,7 +94,8 @@ class ClockSampler:
 
 
 def contraction_units(L, spins):
-    """(l, m, m' >= 0, map) multiply-accumulates of one direction's Delta contraction."""
+    """(l, m, m' >= 0, map) real-kernel x complex multiply-accumulates of one
+    direction's Delta contraction (4 flops each)."""
     tot = 0
     for s in spins:
         for l in range(abs(s), L):
@@ -103,11 +104,26 @@ def contraction_units(L, spins):
 
 
 def risbo_units(L):
-    """Quarter-plane element updates of one Risbo sweep (two half steps per l)."""
+    """Stencil evaluations of one Risbo sweep that the pi/2 symmetries leave
+    necessary: the lower triangle of the half-integer plane (l entries a side)
+    and of the integer plane (l + 1) for every l = 1 .. L-1 (7 flops each:
+    4 multiplies and 3 adds)."""
     tot = 0
     for l in range(1, L):
-        tot += l * l + (l + 1) * (l + 1)
+        tot += l * (l + 1) // 2 + (l + 1) * (l + 2) // 2
     return tot
+
+
+def fft_stage_bytes(L, B, precision):
+    """Algorithmic HBM bytes of the FFT stages of one round trip (inverse +
+    forward): every stage boundary written once and read once."""
+    M = 2 * L - 1
+    nmw = (L - 1) * M + 1
+    cf = 8 if precision == "mixed" else 16      # G_m(theta_t) buffers
+    gp_f = 8 if precision == "mixed" else 16    # G+ (forward contraction input)
+    phi = B * (nmw * 16 + M * L * cf) * 2       # phi forward + phi inverse
+    theta = B * (M * L * cf + M * L * gp_f) + B * (M * L * 16 + M * L * cf)  # theta forward + theta inverse
+    return {"phi": phi, "theta": theta}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -197,28 +213,38 @@ def run_ours(args, rank, world, local_rank):
     bytes_flm = B * L * L * 16
     bytes_map = B * mw.map_size(L) * 16
 
-    # roofline of the dominant stage
+    # rooflines: every stage against its own bound; the dominant one is "roofline"
     pk = peaks()
+    steps = args.steps
+    fb = fft_stage_bytes(L, B, args.precision)
+    stage_roof = {}
+    t = {k: v[0] / 1e3 for k, v in stages.items()}  # seconds over the timed steps
+    if t["delta"] > 0:
+        fl = 2 * steps * risbo_units(L) * 7
+        a = fl / t["delta"] / 1e12
+        stage_roof["delta"] = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                               "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep",
+                               "peak_src": "measured (own FP64 DFMA microbenchmark)"}
+    if t["contract"] > 0:
+        fl = 2 * steps * contraction_units(L, spins) * 4
+        a = fl / t["contract"] / 1e12
+        if args.precision == "mixed":
+            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                      "frac": a / pk["bf16_tflops"], "kernel": "k_tc_forward/k_tc_inverse",
+                                      "peak_src": "measured (MEASURED_PEAKS.json bf16 dense burst)"}
+        else:
+            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": 4.0, "unit": "TFLOP/s",
+                                      "frac": a / 4.0, "kernel": "k_dmma_forward/k_dmma_inverse",
+                                      "peak_src": "measured (own FP64 mma.sync microbenchmark)"}
+    for k in ("theta", "phi"):
+        if t[k] > 0:
+            a = steps * fb[k] / t[k] / 1e9
+            stage_roof[k] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                             "frac": a / pk["hbm_gbs"], "peak_src": pk["src"]}
     dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k][0])
-    t_dom_s = stages[dom][0] / 1e3
-    if dom == "contract":
-        flops = 2 * args.steps * contraction_units(L, spins) * 4  # complex x real MAC = 4 flops
-        achieved = flops / t_dom_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["fp64_tflops"], "traffic": None, "kernel": "k_contract_forward/inverse",
-                "peak_src": "measured (own FP64 DFMA microbenchmark)"}
-    elif dom == "delta":
-        flops = 2 * args.steps * risbo_units(L) * 7  # 4-point stencil: 4 mul + 3 add
-        achieved = flops / t_dom_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["fp64_tflops"], "traffic": None, "kernel": "k_risbo_half",
-                "peak_src": "measured (own FP64 DFMA microbenchmark)"}
-    else:
-        byts = args.steps * (bytes_flm + bytes_map) * 2
-        achieved = byts / t_dom_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_src": pk["src"]}
+    roof = dict(stage_roof[dom])
+    roof["stage"] = dom
+    roof["traffic"] = None  # DRAM bytes of the current kernel build are in profiles/ when captured
     result = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -233,6 +259,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "roofline": roof,
+        "stage_roofline": stage_roof,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
