@@ -155,6 +155,35 @@ enum { MW_STAGE_PHI = 0, MW_STAGE_THETA = 1, MW_STAGE_DELTA = 2, MW_STAGE_CONTRA
 mw_status mw_plan_set_timing(mw_plan *plan, int enable);
 mw_status mw_plan_stage_times(mw_plan *plan, double *ms, long long *launches, int reset);
 
+/* mw_inverse_noalloc: the inverse transform of ONE map of band limit L and spin
+ * s, FP64 throughout, that allocates no memory at all -- no plan, no
+ * cudaMalloc/cudaFree, no allocating library routine.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory --
+ * code inside a custom allocator's own callbacks (which must not re-enter the
+ * allocator), hosts that forbid allocation after start-up (real-time loops,
+ * where cudaMalloc/cudaFree would also synchronise the device), or processes
+ * that have handed all free device memory to another memory pool.
+ *   flm_in  : L*L complex doubles (layout above), device or managed memory of
+ *             the current device
+ *   map_out : N_MW complex doubles (layout above), device or managed memory of
+ *             the current device; must not overlap flm_in
+ *   stream  : cudaStream_t of the current device (NULL: legacy default stream)
+ * Limits: 1 <= L <= MW_NOALLOC_MAX_L and |s| < L; anything else, host
+ * pointers included, returns MW_EINVAL before anything is enqueued.
+ * Scratch: the Wigner-Delta planes and the F_mm' coefficients live in one
+ * static device array of MW_NOALLOC_SCRATCH_BYTES (about 2.6 MB), which every
+ * GPU that loads libmw holds until the process exits.  The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture begins.
+ * Every call on a device uses the same array and finds the previous call's
+ * contents there (the kernels clear what must start at zero), so calls whose
+ * GPU work overlaps -- two streams, or two host threads -- race and give wrong
+ * results: order them on one stream or with events.  Enqueues two kernels and
+ * returns before the GPU finishes; MW_ECUDA if a CUDA call or launch fails. */
+#define MW_NOALLOC_MAX_L 128
+#define MW_NOALLOC_SCRATCH_BYTES 2601744u
+mw_status mw_inverse_noalloc(int L, int s, const void *flm_in, void *map_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,8 @@ def lib():
         L.mw_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           c_int]
         L.mw_plan_stage_times.restype = c_int
+        L.mw_inverse_noalloc.argtypes = [c_int, c_int, vp, vp, vp]
+        L.mw_inverse_noalloc.restype = c_int
         _lib = L
     return _lib
 
@@ -224,3 +226,29 @@ class RaggedPlan(Plan):
             self.flm_offsets.append(fo)
             mo += map_size(L)
             fo += flm_size(L)
+
+
+NOALLOC_MAX_L = 128
+
+
+def inverse_noalloc(L, s, flm, out):
+    """Inverse transform of one map without any device allocation.
+
+    For callers that cannot allocate device memory (inside a custom
+    allocator's callbacks, hosts that forbid allocation after start-up,
+    processes whose free device memory belongs to another pool): the library
+    keeps every intermediate in one static device array of about 2.6 MB, so
+    the caller provides both buffers.  flm: L*L complex128 on the current CUDA
+    device; out: N_MW complex128 on that device.  L <= NOALLOC_MAX_L.  Calls
+    share the static array, so calls whose GPU work overlaps (two streams or
+    threads) race; the first call on a device looks the array up and should
+    precede any stream capture.  Returns out.
+    """
+    for name, t, n in (("flm", flm, flm_size(L)), ("out", out, map_size(L))):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name}: expected a contiguous complex128 CUDA tensor of {n} elements")
+    st = lib().mw_inverse_noalloc(int(L), int(s), ctypes.c_void_p(flm.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  _stream_of(flm))
+    if st != MW_OK:
+        raise MWError(st, f"mw_inverse_noalloc(L={L}, s={s}; at most L={NOALLOC_MAX_L})")
+    return out
