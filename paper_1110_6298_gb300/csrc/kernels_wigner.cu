@@ -154,19 +154,17 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
       while ((I + 1) * (I + 2) / 2 <= t) ++I;
       const int J = t - I * (I + 1) / 2;
       const int a0 = I * kRT, b0 = J * kRT;
-      if (tid == 0) {
+      if (tid < 32) {  // lanes 0..8 each wait for one neighbour, concurrently
         int ok = 1;
-        if (l > l_begin) {
-          for (int di = -1; di <= 1 && ok; ++di)
-            for (int dj = -1; dj <= 1 && ok; ++dj) {
-              const int Ii = I + di, Jj = J + dj;
-              if (Ii < 0 || Jj < 0 || Ii >= Tp || Jj >= Tp) continue;  // not part of plane l-1
-              const int hi = Ii > Jj ? Ii : Jj, lo = Ii > Jj ? Jj : Ii;
-              if (!wait_tile(A.prog, tile_index(hi, lo), l - 1)) { ok = 0; atomicOr(A.err, 2); }
-            }
+        if (l > l_begin && tx < 9) {
+          const int Ii = I + tx / 3 - 1, Jj = J + tx % 3 - 1;
+          if (Ii >= 0 && Jj >= 0 && Ii < Tp && Jj < Tp) {  // part of plane l-1
+            const int hi = Ii > Jj ? Ii : Jj, lo = Ii > Jj ? Jj : Ii;
+            if (!wait_tile(A.prog, tile_index(hi, lo), l - 1)) { ok = 0; atomicOr(A.err, 2); }
+          }
         }
-        if (ok && *(volatile int*)A.err) ok = 0;
-        s_ok = ok;
+        ok = __all_sync(0xffffffffu, ok);
+        if (tx == 0) s_ok = ok && !*(volatile int*)A.err;
       }
       __syncthreads();
       if (!s_ok) return;
@@ -190,9 +188,9 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
       // Row segments: the product sqrt(j'-mu) d_{+,jp} of column c is the
       // sqrt(j'-mu) d_{+,jm} of column c+1, so it is carried along (5 FP64
       // instructions per element).
-      for (int task = tid; task < (kRT + 1) * 4; task += kRThreads) {
+      for (int task = tid; task < (kRT + 1) * 7; task += kRThreads) {
         const int r = task % (kRT + 1), seg = task / (kRT + 1);
-        const int c0 = seg * 9, c1 = min(c0 + 9, kRT + 1);  // 9, 9, 9, 6 columns
+        const int c0 = seg * 5, c1 = min(c0 + 5, kRT + 1);  // six segments of 5 columns, one of 3
         const int i = a0 - 1 + r;
         if (i >= nh) {
           for (int c = c0; c < c1; ++c) hh[r][c] = 0.0;
