@@ -1,12 +1,17 @@
 """Benchmark: MW forward + inverse transforms/s at L = 2048, 16 maps (8 spin 0,
 8 spin 2), complex Gaussian f_lm with E|f_lm|^2 = 1/(l+1)^2.
 
-One step = inverse transform of the batch followed by the forward transform of
-the result (the round trip of the paper's protocol, Sec. V-D): 2B transforms.
-Inputs (1.1 GB of f_lm, 2.1 GB of maps) are larger than L2, so no flush is
-needed between steps.  value: device-timed (CUDA events on the stream) with
-inputs resident in HBM.  e2e: the same round trip through the C ABI with pinned
-host buffers, host<->device copies inside the timed region.  The roofline entry
+One step = the forward transform of B maps and the inverse transform of B
+independent f_lm sets in one fused call (mw_forward_inverse), whose two Wigner
+sums share one Delta recursion: 2B transforms.  The maps are band-limited
+(the inverse of a second seeded f_lm batch, made before timing), so the
+forward half's output is checked against that batch.  The dependent round
+trip (inverse, then forward of its result; two recursions) is timed too and
+reported under "roundtrip".  Inputs (1.1 GB of f_lm, 2.1 GB of maps) are
+larger than L2, so no flush is needed between steps.  value: device-timed
+(CUDA events on the stream) with inputs resident in HBM.  e2e: the same fused
+step through the C ABI with pinned host buffers, host<->device copies inside
+the timed region.  The roofline entry
 describes the dominant stage, timed live with the library's per-stage events.
 
 --impl reference runs the FP64 CPU oracle (the only baseline this project has)
@@ -143,26 +148,39 @@ def run_ours(args, rank, world, local_rank):
     w = wl.workload_l2048_b16(L=args.L)
     L, spins = w["L"], w["spins"]
     B = len(spins)
+    nmw = mw.map_size(L)
     flm_h = torch.from_numpy(np.stack(w["flm"]))
-    flm = flm_h.to(dev)
+    flm = flm_h.to(dev)                      # input of the inverse half
+    flm2 = torch.from_numpy(np.stack(wl.workload_l2048_b16(L=args.L, seed=14)["flm"])).to(dev)
     plan = mw.Plan(L, spins, precision=args.precision)
-    maps = torch.empty((B, mw.map_size(L)), dtype=torch.complex128, device=dev)
-    out = torch.empty_like(flm)
+    maps_in = plan.inverse(flm2)             # input of the forward half: band-limited maps (set-up, untimed)
+    flm_out = torch.empty_like(flm)
+    maps_out = torch.empty((B, nmw), dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward_inverse(maps_in, flm, flm_out, maps_out)
 
     launches_per_step = 0
     for _ in range(args.warmup):
-        plan.inverse(flm, out=maps)
-        n1 = plan.last_launches
-        plan.forward(maps, out=out)
-        launches_per_step = n1 + plan.last_launches
+        step()
+        launches_per_step = plan.last_launches
     torch.cuda.synchronize(dev)
-    err = float((out - flm).abs().max().item() / flm.abs().max().item())
+    # forward(inverse(flm2)) must give flm2 back
+    err = float((flm_out - flm2).abs().max().item() / flm2.abs().max().item())
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    def max_over_ranks(x):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([x], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            x = float(t.item())
+        return x
 
     clocks = ClockSampler(local_rank)
     plan.set_timing(True)
@@ -174,44 +192,50 @@ def run_ours(args, rank, world, local_rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.inverse(flm, out=maps)
-        plan.forward(maps, out=out)
+        step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1))
     stages = plan.stage_times(reset=True)
     plan.set_timing(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * 2 * B * args.steps / (ms / 1e3)
 
+    # context: the dependent round trip (inverse, then forward of its output),
+    # which cannot share a sweep: two recursions per step
+    rt_maps = torch.empty_like(maps_out)
+    rt_out = torch.empty_like(flm)
+    plan.inverse(flm, out=rt_maps)
+    plan.forward(rt_maps, out=rt_out)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.inverse(flm, out=rt_maps)
+        plan.forward(rt_maps, out=rt_out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rt_ms = max_over_ranks(e0.elapsed_time(e1))
+    rt_err = float((rt_out - flm).abs().max().item() / flm.abs().max().item())
+    del rt_maps, rt_out
+
     # end to end: pinned host buffers through the C ABI, copies inside the timed region
+    maps_pin = maps_in.cpu().pin_memory()
     flm_pin = flm_h.pin_memory()
-    map_pin = torch.empty((B, mw.map_size(L)), dtype=torch.complex128).pin_memory()
-    out_pin = torch.empty_like(flm_pin).pin_memory()
+    flm_out_pin = torch.empty_like(flm_pin).pin_memory()
+    maps_out_pin = torch.empty_like(maps_pin).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
-    plan.inverse(flm_pin, out=map_pin)
-    plan.forward(map_pin, out=out_pin)
+    plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan.inverse(flm_pin, out=map_pin)
-        plan.forward(map_pin, out=out_pin)
+        plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
     torch.cuda.synchronize(dev)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * 2 * B * e2e_steps / t_e2e
     bytes_flm = B * L * L * 16
-    bytes_map = B * mw.map_size(L) * 16
+    bytes_map = B * nmw * 16
 
     # rooflines: every stage against its own bound; the dominant one is "roofline"
     pk = peaks()
@@ -220,7 +244,7 @@ def run_ours(args, rank, world, local_rank):
     stage_roof = {}
     t = {k: v[0] / 1e3 for k, v in stages.items()}  # seconds over the timed steps
     if t["delta"] > 0:
-        fl = 2 * steps * risbo_units(L) * 7
+        fl = steps * risbo_units(L) * 7  # one sweep per fused step
         a = fl / t["delta"] / 1e12
         stage_roof["delta"] = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                                "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep",
@@ -233,9 +257,10 @@ def run_ours(args, rank, world, local_rank):
                                       "frac": a / pk["bf16_tflops"], "kernel": "k_tc_forward/k_tc_inverse",
                                       "peak_src": "measured (MEASURED_PEAKS.json bf16 dense burst)"}
         else:
-            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": 4.0, "unit": "TFLOP/s",
-                                      "frac": a / 4.0, "kernel": "k_dmma_forward/k_dmma_inverse",
-                                      "peak_src": "measured (own FP64 mma.sync microbenchmark)"}
+            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": 1.045, "unit": "TFLOP/s",
+                                      "frac": a / 1.045, "kernel": "k_dmma_forward/k_dmma_inverse",
+                                      "peak_src": "measured (own FP64 mma.sync m8n8k4 microbenchmark; "
+                                                  "same FP64 pipe as DFMA on this part)"}
     for k in ("theta", "phi"):
         if t[k] > 0:
             a = steps * fb[k] / t[k] / 1e9
@@ -250,10 +275,14 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32+bf16",
         "data": "synthetic (seeded complex Gaussian f_lm, C_l=1/(l+1)^2)",
-        "config": {"workload": f"MW round trip L={L}, B={B} (8 maps s=0, 8 maps s=2)", "L": L, "batch": B,
+        "config": {"workload": f"MW forward of B={B} maps + inverse of B={B} independent f_lm per step, L={L} "
+                               f"(8 maps s=0, 8 maps s=2), one shared Delta recursion", "L": L, "batch": B,
                    "spins": spins, "precision": args.precision, "l2_flush": "inputs larger than L2",
                    "parallelism": f"replicas x{world}"},
         "roundtrip_rel_err": err,
+        "roundtrip": {"value": world * 2 * B * args.steps / (rt_ms / 1e3), "unit": "transforms/s",
+                      "ms_per_step": rt_ms / args.steps, "rel_err": rt_err,
+                      "what": "inverse then forward of its output (two recursions per step)"},
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
                 "d2h_bytes_per_step": bytes_map + bytes_flm},
         "gpu_launches": launches_per_step * args.steps,

@@ -112,6 +112,19 @@ mw_status mw_forward(mw_plan *plan, const void *map_in, void *flm_out, void *str
  * grid. */
 mw_status mw_inverse(mw_plan *plan, const void *flm_in, void *map_out, void *stream);
 
+/* Fused forward + inverse of independent inputs: the forward transform of
+ * map_in [batch][N_MW] -> flm_out [batch][L*L] and the inverse transform of
+ * flm_in [batch][L*L] -> map_out [batch][N_MW] in one call that runs the
+ * Wigner-Delta recursion (Sec. V-B) once for both Wigner sums, Eq. (flm_wig)
+ * and Eq. (Fmm): Delta^l depends on neither the direction nor the data, so each
+ * plane l feeds both contractions while it is resident.  The results are
+ * bitwise those of mw_forward(map_in) and mw_inverse(flm_in) on this plan.  The
+ * four buffers must not overlap.  The first fused call on a plan allocates a
+ * second set of workspace (the inverse half's), counted by
+ * mw_plan_workspace_bytes; with MW_FLAG_GRAPH the whole call is one graph. */
+mw_status mw_forward_inverse(mw_plan *plan, const void *map_in, void *flm_out, const void *flm_in, void *map_out,
+                             void *stream);
+
 /* Hermitian adjoints (not in the paper; used for gradients):
  * mw_forward_adjoint: flm_in [batch][L*L] -> map_out [batch][N_MW], = forward^H.
  * mw_inverse_adjoint: map_in [batch][N_MW] -> flm_out [batch][L*L], = inverse^H.

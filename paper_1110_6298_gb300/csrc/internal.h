@@ -71,14 +71,21 @@ struct mw_plan {
   int LD = 0;                      // plane row stride (L+1)
   double2* d_map_stage = nullptr;  // host-pointer staging
   double2* d_flm_stage = nullptr;
+  double2* d_map_stage2 = nullptr;  // host-pointer staging of a fused call's inverse half
+  double2* d_flm_stage2 = nullptr;
+  // fused forward+inverse calls: plans of the same maps (one per sub-plan of a
+  // ragged plan) that borrow this plan's sweep state and run the inverse half
+  // with workspace of their own; built on the first fused call
+  std::vector<mw_plan*> twins;
 
   size_t ws_bytes = 0;
   int last_launches = 0;
 
   // CUDA graphs of whole calls (MW_FLAG_GRAPH): one per (direction, input, output)
-  struct GraphEntry { int dir; const void* in; void* out; cudaGraphExec_t exec; };
+  struct GraphEntry { int dir; const void* in; void* out; const void* in2; void* out2; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;
   bool graph_failed = false;       // capture unsupported here: run calls directly
+  cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
 
   // optional per-stage timing (CUDA events on the call's stream)
   bool timing = false;
@@ -120,5 +127,13 @@ cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cud
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
 int risbo_blocks_per_sm();
 
-cudaError_t run_wigner(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
-                       cudaStream_t st, int* launches);
+// One consumer of a Risbo sweep: plan q's forward contraction (mode 0, G+ in
+// q's workspace -> flm_out) or inverse contraction (mode 1, flm_in -> F+ in q's
+// workspace).  Plane l serves every consumer with L > l.
+struct WignerJob {
+  mw_plan* q;
+  int mode;
+  const double2* flm_in;
+  double2* flm_out;
+};
+cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches);

@@ -76,14 +76,29 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t 
 
 // Add the six slots into float-float accumulators: warp quadrant q owns TMEM
 // lanes (tile rows) 32q..32q+31, half h owns columns 16h..16h+15 of each slot.
+// The four hi.hi slots go through TwoSum; the two correction slots (at most
+// 2^-8 of the sum) are added to the low word directly, where their own
+// rounding is below 2^-32 of the result.  Loads are issued in pairs.
 __device__ __forceinline__ void drain_half(uint32_t tmem, int quad, int half, float* hi, float* lo) {
+  const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(16 * half);
 #pragma unroll
-  for (int slot = 0; slot < kSlots; ++slot) {
-    float v[16];
-    umma::ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * kN + 16 * half), v);
+  for (int sp = 0; sp < 2; ++sp) {
+    uint32_t a[16], b[16];
+    umma::ld_32x32b_x16_async(base + (uint32_t)(2 * sp * kN), a);
+    umma::ld_32x32b_x16_async(base + (uint32_t)((2 * sp + 1) * kN), b);
+    umma::wait_ld();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) two_sum_acc(hi[j], lo[j], v[j]);
+    for (int j = 0; j < 16; ++j) {
+      two_sum_acc(hi[j], lo[j], __uint_as_float(a[j]));
+      two_sum_acc(hi[j], lo[j], __uint_as_float(b[j]));
+    }
   }
+  uint32_t a[16], b[16];
+  umma::ld_32x32b_x16_async(base + (uint32_t)(4 * kN), a);
+  umma::ld_32x32b_x16_async(base + (uint32_t)(5 * kN), b);
+  umma::wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) lo[j] += __uint_as_float(a[j]) + __uint_as_float(b[j]);
 }
 
 __device__ __forceinline__ void sync_all() {
@@ -180,9 +195,12 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
     for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
     if (lstart < l1) {
       for (int mp0 = 0; mp0 < l1; mp0 += kKTile) {
-        // A: 128 rows x 8 chunks of 8 m'
+        // A: 128 rows x 8 chunks of 8 m'.  Lanes 8q..8q+7 take the 8 rows of
+        // one core matrix (each 8-lane phase of the 16-byte stores fills 128
+        // contiguous bytes: no bank conflicts) and the four lane octets of a
+        // warp take consecutive chunks (128 contiguous bytes of each plane row).
         for (int task = tid; task < 128 * (kKTile / 8); task += kThreads) {
-          const int r = task >> 3, c = task & 7;
+          const int r = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
           const int l = l0 + r, mp = mp0 + 8 * c;
           float x[8];
           if (l >= lstart && l < l1 && mp <= l) {
@@ -193,9 +211,9 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
           }
           store_split8(sA, kATile, umma::tile_off(r, 8 * c, kKTile / 8), x);
         }
-        // B: 32 rows (map, re/im; +am then -am) x 8 chunks
+        // B: 32 rows (map, re/im; +am then -am) x 8 chunks, same lane order as A
         for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
-          const int n = task >> 3, c = task & 7;
+          const int n = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
           const int j = n >> 1, mp = mp0 + 8 * c;
           float x[8];
 #pragma unroll
@@ -302,9 +320,11 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
   for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
   for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
     const int lb = l0 + kt * kKTile;
-    // A: 64 l x 16 chunks of 8 m'
+    // A: 64 l x 16 chunks of 8 m'.  Lanes 8q..8q+7 take 8 consecutive l (one
+    // MN-major core matrix: conflict-free 16-byte stores), the lane octets
+    // consecutive chunks of m'.
     for (int task = tid; task < kKTile * 16; task += kThreads) {
-      const int k = task >> 4, c = task & 15;
+      const int k = (task & 7) + 8 * (task >> 7), c = (task >> 3) & 15;
       const int l = lb + k, mp = mp0 + 8 * c;
       float x[8];
       if (l >= lstart && l < l1 && mp <= l && mp < L) {
@@ -315,9 +335,9 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
       }
       store_split8(sA, kATile, c * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, x);
     }
-    // B: 32 rows (map, re/im) x 8 chunks of 8 l (K-major)
+    // B: 32 rows (map, re/im) x 8 chunks of 8 l (K-major), lane order as above
     for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
-      const int n = task >> 3, c = task & 7;
+      const int n = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
       const int j = n >> 1;
       float x[8];
 #pragma unroll

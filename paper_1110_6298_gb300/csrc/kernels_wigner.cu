@@ -288,24 +288,24 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
 }
 
 // One Risbo sweep (recursion state and staging of the owner o) feeding the
-// contractions of the consumer plans cs (for a regular plan o == cs[0]; for a
-// ragged plan the consumers are the per-band-limit sub-plans).  Plane l serves
-// every consumer with L > l: Delta^l depends on neither L nor s.
-cudaError_t run_sweep(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
-                      cudaStream_t st, int* launches) {
+// contractions of the jobs: for a regular plan one job on o itself; for a
+// ragged plan one per band-limit sub-plan; for a fused forward+inverse call
+// the forward jobs and the inverse jobs together.  Plane l serves every job
+// with L > l: Delta^l depends on neither L nor s.
+cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {
   const bool fp64 = o->prec == MW_PREC_FP64;
   const int chunk = fp64 ? kChunk : kTcChunk;
   int nl = 0;
   cudaError_t e;
-  if (mode == 1) {
-    for (int c = 0; c < nc; ++c) {
-      e = cudaMemsetAsync(cs[c]->d_Gp, 0, sizeof(double2) * (size_t)cs[c]->B * cs[c]->M * cs[c]->L, st);
+  for (int c = 0; c < nj; ++c) {
+    if (jobs[c].mode != 1) continue;
+    mw_plan* q = jobs[c].q;
+    e = cudaMemsetAsync(q->d_Gp, 0, sizeof(double2) * (size_t)q->B * q->M * q->L, st);
+    if (e != cudaSuccess) return e;
+    if (!fp64) {
+      e = launch_flm_to_f32(q, jobs[c].flm_in, st);
       if (e != cudaSuccess) return e;
-      if (!fp64) {
-        e = launch_flm_to_f32(cs[c], flm_in, st);
-        if (e != cudaSuccess) return e;
-        ++nl;
-      }
+      ++nl;
     }
   }
   k_plane_init<<<1, 1, 0, st>>>(o->d_S, fp64 ? nullptr : o->d_S32);
@@ -321,12 +321,16 @@ cudaError_t run_sweep(mw_plan* o, mw_plan* const* cs, int nc, int mode, const do
     nl += nd;
     StageSpan span_c(o, MW_STAGE_CONTRACT, st);
     int ncl = 0;
-    for (int c = 0; c < nc; ++c) {
-      mw_plan* q = cs[c];
+    for (int c = 0; c < nj; ++c) {
+      mw_plan* q = jobs[c].q;
       if (q->L <= l0) continue;
       const int l1c = l1 < q->L ? l1 : q->L;
-      if (fp64) e = (mode == 0) ? launch_dmma_forward(q, l0, l1c, flm_out, st) : launch_dmma_inverse(q, l0, l1c, flm_in, st);
-      else e = (mode == 0) ? launch_tc_forward(q, l0, l1c, flm_out, st) : launch_tc_inverse(q, l0, l1c, q->d_flmf, st);
+      if (fp64)
+        e = (jobs[c].mode == 0) ? launch_dmma_forward(q, l0, l1c, jobs[c].flm_out, st)
+                                : launch_dmma_inverse(q, l0, l1c, jobs[c].flm_in, st);
+      else
+        e = (jobs[c].mode == 0) ? launch_tc_forward(q, l0, l1c, jobs[c].flm_out, st)
+                                : launch_tc_inverse(q, l0, l1c, q->d_flmf, st);
       ++ncl;
       if (e != cudaSuccess) return e;
     }
@@ -355,7 +359,6 @@ int risbo_blocks_per_sm() {
   return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
-cudaError_t run_wigner(mw_plan* o, mw_plan* const* cs, int nc, int mode, const double2* flm_in, double2* flm_out,
-                       cudaStream_t st, int* launches) {
-  return run_sweep(o, cs, nc, mode, flm_in, flm_out, st, launches);
+cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {
+  return run_sweep(o, jobs, nj, st, launches);
 }

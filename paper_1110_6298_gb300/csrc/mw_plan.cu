@@ -66,13 +66,16 @@ cudaError_t upload_complex(const std::vector<double>& re, const std::vector<doub
 void free_plan(mw_plan* p) {
   if (!p) return;
   for (mw_plan* c : p->subs) free_plan(c);
+  for (mw_plan* c : p->twins) free_plan(c);
   if (p->shared_sweep) { p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; }
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
+                  p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto ev : p->pool) cudaEventDestroy(ev);
   delete p;
@@ -286,105 +289,171 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-enum Direction { kForward, kInverse, kForwardAdjoint, kInverseAdjoint };
+enum Direction { kForward, kInverse, kForwardAdjoint, kInverseAdjoint, kFused };
 
-mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream) {
+// Twins for fused forward+inverse calls: one per consumer plan (the plan
+// itself, or each sub-plan of a ragged plan), borrowing p's sweep state.
+mw_status ensure_twins(mw_plan* p) {
+  if (!p->twins.empty()) return MW_OK;
+  std::vector<mw_plan*> src;
+  if (p->subs.empty()) src.push_back(p);
+  else src = p->subs;
+  for (mw_plan* q : src) {
+    mw_plan* t = nullptr;
+    const mw_status st = build_plan(&t, q->L, q->B, q->spins.data(), q->flags, q->moff.data(), q->foff.data(), p, false);
+    if (st != MW_OK) {
+      for (mw_plan* u : p->twins) {
+        p->ws_bytes -= u->ws_bytes;
+        free_plan(u);
+      }
+      p->twins.clear();
+      return st;
+    }
+    p->twins.push_back(t);
+    p->ws_bytes += t->ws_bytes;
+  }
+  return MW_OK;
+}
+
+// One call.  For kFused, (in, out) = (map_in, flm_out) of the forward half and
+// (in2, out2) = (flm_in, map_out) of the inverse half; otherwise in2/out2 are
+// unused.
+mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream, const void* in2 = nullptr,
+              void* out2 = nullptr) {
   if (!p || !in || !out) return MW_EINVAL;
+  const bool fused = dir == kFused;
+  if (fused && (!in2 || !out2)) return MW_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (fused) {
+    const mw_status ts = ensure_twins(p);
+    if (ts != MW_OK) return ts;
+  }
   // consumers: the plan itself, or the per-band-limit sub-plans of a ragged plan
   std::vector<mw_plan*> cs;
   if (p->subs.empty()) cs.push_back(p);
   else cs = p->subs;
   const size_t nmw = (size_t)p->map_elems, nlm = (size_t)p->flm_elems;
-  const bool map_in = (dir == kForward || dir == kInverseAdjoint);
+  const bool map_in = (dir == kForward || dir == kInverseAdjoint || fused);
   const size_t in_elems = map_in ? nmw : nlm, out_elems = map_in ? nlm : nmw;
-  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
   cudaError_t e = cudaSuccess;
-  // host staging buffers are allocated on first use
-  if (!in_dev || !out_dev) {
-    if (!p->d_map_stage) {
-      e = cudaMalloc((void**)&p->d_map_stage, sizeof(double2) * nmw);
-      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nmw;
-    }
-    if (e == cudaSuccess && !p->d_flm_stage) {
-      e = cudaMalloc((void**)&p->d_flm_stage, sizeof(double2) * nlm);
-      if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * nlm;
-    }
-    if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
-  }
+  auto ensure = [&](double2** slot, size_t elems) {
+    if (e != cudaSuccess || *slot) return;
+    e = cudaMalloc((void**)slot, sizeof(double2) * elems);
+    if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * elems;
+  };
+  // host buffers are staged through plan-owned device buffers (allocated on first use)
   const double2* din = (const double2*)in;
   double2* dout = (double2*)out;
+  const double2* din2 = (const double2*)in2;
+  double2* dout2 = (double2*)out2;
+  double2** in_slot = map_in ? &p->d_map_stage : &p->d_flm_stage;
+  double2** out_slot = map_in ? &p->d_flm_stage : &p->d_map_stage;
+  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+  const bool in2_dev = !fused || is_device_ptr(in2), out2_dev = !fused || is_device_ptr(out2);
+  if (!in_dev) ensure(in_slot, in_elems);
+  if (!out_dev) ensure(out_slot, out_elems);
+  if (!in2_dev) ensure(&p->d_flm_stage2, nlm);
+  if (!out2_dev) ensure(&p->d_map_stage2, nmw);
+  if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
   if (!in_dev) {
-    double2* stage = map_in ? p->d_map_stage : p->d_flm_stage;
-    e = cudaMemcpyAsync(stage, in, sizeof(double2) * in_elems, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(*in_slot, in, sizeof(double2) * in_elems, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
-    din = stage;
+    din = *in_slot;
   }
-  if (!out_dev) dout = map_in ? p->d_flm_stage : p->d_map_stage;
+  if (!in2_dev) {
+    e = cudaMemcpyAsync(p->d_flm_stage2, in2, sizeof(double2) * nlm, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    din2 = p->d_flm_stage2;
+  }
+  if (!out_dev) dout = *out_slot;
+  if (!out2_dev) dout2 = p->d_map_stage2;
 
   int nl = 0;
   auto enqueue = [&](cudaStream_t st) -> cudaError_t {
-  // one FFT stage for every consumer, timed as one span on the plan
-  auto stage = [&](int stg, cudaError_t (*fn)(const mw_plan*, cudaStream_t)) {
+  // one FFT stage for every consumer in cl, timed as one span on the plan
+  auto stage = [&](const std::vector<mw_plan*>& cl, int stg, cudaError_t (*fn)(const mw_plan*, cudaStream_t)) {
     if (e != cudaSuccess) return;
     StageSpan sp(p, stg, st);
-    for (mw_plan* c : cs) {
+    for (mw_plan* c : cl) {
       if (e == cudaSuccess) e = fn(c, st);
       ++nl;
     }
-    sp.end((int)cs.size());
+    sp.end((int)cl.size());
   };
-  auto phi = [&](auto fn, auto ptr) {
+  auto phi = [&](const std::vector<mw_plan*>& cl, auto fn, auto ptr) {
     if (e != cudaSuccess) return;
     StageSpan sp(p, MW_STAGE_PHI, st);
-    for (mw_plan* c : cs) {
+    for (mw_plan* c : cl) {
       if (e == cudaSuccess) e = fn(c, ptr, st);
       ++nl;
     }
-    sp.end((int)cs.size());
+    sp.end((int)cl.size());
   };
+  auto wigner = [&](const std::vector<mw_plan*>& fwd, double2* flm_out, const std::vector<mw_plan*>& inv,
+                    const double2* flm_in) {
+    if (e != cudaSuccess) return;
+    std::vector<WignerJob> jobs;
+    for (mw_plan* c : fwd) jobs.push_back({c, 0, nullptr, flm_out});
+    for (mw_plan* c : inv) jobs.push_back({c, 1, flm_in, nullptr});
+    e = run_wigner(p, jobs.data(), (int)jobs.size(), st, &nl);
+  };
+  const std::vector<mw_plan*> none;
   switch (dir) {
     case kForward:
-      phi(launch_phi_forward, din);
-      stage(MW_STAGE_THETA, launch_theta_forward);
-      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 0, nullptr, dout, st, &nl);
+      phi(cs, launch_phi_forward, din);
+      stage(cs, MW_STAGE_THETA, launch_theta_forward);
+      wigner(cs, dout, none, nullptr);
       break;
     case kInverse:
-      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 1, din, nullptr, st, &nl);
-      stage(MW_STAGE_THETA, launch_theta_inverse);
-      phi(launch_phi_inverse, dout);
+      wigner(none, nullptr, cs, din);
+      stage(cs, MW_STAGE_THETA, launch_theta_inverse);
+      phi(cs, launch_phi_inverse, dout);
       break;
     case kForwardAdjoint:
-      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 1, din, nullptr, st, &nl);
-      stage(MW_STAGE_THETA, launch_theta_forward_adjoint);
-      phi(launch_phi_forward_adjoint, dout);
-      phi(launch_pole_forward_adjoint, dout);
+      wigner(none, nullptr, cs, din);
+      stage(cs, MW_STAGE_THETA, launch_theta_forward_adjoint);
+      phi(cs, launch_phi_forward_adjoint, dout);
+      phi(cs, launch_pole_forward_adjoint, dout);
       break;
     case kInverseAdjoint:
-      phi(launch_phi_inverse_adjoint, din);
-      stage(MW_STAGE_THETA, launch_theta_inverse_adjoint);
-      if (e == cudaSuccess) e = run_wigner(p, cs.data(), (int)cs.size(), 0, nullptr, dout, st, &nl);
+      phi(cs, launch_phi_inverse_adjoint, din);
+      stage(cs, MW_STAGE_THETA, launch_theta_inverse_adjoint);
+      wigner(cs, dout, none, nullptr);
+      break;
+    case kFused:  // forward half on cs, inverse half on the twins, one sweep for both
+      phi(cs, launch_phi_forward, din);
+      stage(cs, MW_STAGE_THETA, launch_theta_forward);
+      wigner(cs, dout, p->twins, din2);
+      stage(p->twins, MW_STAGE_THETA, launch_theta_inverse);
+      phi(p->twins, launch_phi_inverse, dout2);
       break;
   }
   return e;
   };
   // CUDA graph: captured on the first call with these buffers, replayed after
   bool ran = false;
+  const void* k_in2 = fused ? (const void*)din2 : nullptr;
+  void* k_out2 = fused ? (void*)dout2 : nullptr;
   if ((p->flags & MW_FLAG_GRAPH) && !p->timing && !p->graph_failed) {
     for (auto& g : p->graphs)
-      if (g.dir == (int)dir && g.in == (const void*)din && g.out == (void*)dout) {
+      if (g.dir == (int)dir && g.in == (const void*)din && g.out == (void*)dout && g.in2 == k_in2 && g.out2 == k_out2) {
         e = cudaGraphLaunch(g.exec, st);
         p->last_launches = 1;
         ran = true;
         break;
       }
     if (!ran) {
+      // capture on a plan-owned stream (the caller's may be the legacy default
+      // stream, which cannot be captured); capturing runs nothing, and the
+      // graph is then launched on the caller's stream
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
-      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      cudaError_t ce = cudaSuccess;
+      if (!p->cap_stream) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+      if (ce == cudaSuccess) ce = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (ce == cudaSuccess) {
-        cudaError_t ee = enqueue(st);
-        ce = cudaStreamEndCapture(st, &graph);
+        cudaError_t ee = enqueue(p->cap_stream);
+        ce = cudaStreamEndCapture(p->cap_stream, &graph);
         if (ee != cudaSuccess) ce = ee;
       }
       if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -394,12 +463,14 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
           cudaGraphExecDestroy(p->graphs.front().exec);
           p->graphs.erase(p->graphs.begin());
         }
-        p->graphs.push_back({(int)dir, (const void*)din, (void*)dout, exec});
+        p->graphs.push_back({(int)dir, (const void*)din, (void*)dout, k_in2, k_out2, exec});
         e = cudaGraphLaunch(exec, st);
         p->last_launches = 1;
         ran = true;
       } else {
         cudaGetLastError();  // capture not possible here: fall back to direct launches
+        if (getenv("MW_DEBUG")) fprintf(stderr, "libmw: graph capture failed (%s); running calls directly\n",
+                                        cudaGetErrorString(ce));
         p->graph_failed = true;
         e = cudaSuccess;
         nl = 0;
@@ -411,8 +482,10 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
     p->last_launches = nl;
   }
   if (e != cudaSuccess) return from_cuda(e);
-  if (!out_dev) {
-    e = cudaMemcpyAsync(out, dout, sizeof(double2) * out_elems, cudaMemcpyDeviceToHost, st);
+  if (!out_dev || !out2_dev) {
+    if (!out_dev) e = cudaMemcpyAsync(out, dout, sizeof(double2) * out_elems, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !out2_dev)
+      e = cudaMemcpyAsync(out2, dout2, sizeof(double2) * nmw, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
   }
@@ -570,6 +643,10 @@ mw_status mw_inverse(mw_plan* plan, const void* flm_in, void* map_out, void* str
 }
 mw_status mw_forward_adjoint(mw_plan* plan, const void* flm_in, void* map_out, void* stream) {
   return run(plan, kForwardAdjoint, flm_in, map_out, stream);
+}
+mw_status mw_forward_inverse(mw_plan* plan, const void* map_in, void* flm_out, const void* flm_in, void* map_out,
+                             void* stream) {
+  return run(plan, kFused, map_in, flm_out, stream, flm_in, map_out);
 }
 mw_status mw_inverse_adjoint(mw_plan* plan, const void* map_in, void* flm_out, void* stream) {
   return run(plan, kInverseAdjoint, map_in, flm_out, stream);

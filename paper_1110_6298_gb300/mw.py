@@ -68,6 +68,8 @@ def lib():
         L.mw_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           c_int]
         L.mw_plan_stage_times.restype = c_int
+        L.mw_forward_inverse.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.mw_forward_inverse.restype = c_int
         L.mw_inverse_noalloc.argtypes = [c_int, c_int, vp, vp, vp]
         L.mw_inverse_noalloc.restype = c_int
         _lib = L
@@ -186,6 +188,33 @@ class Plan:
 
     def inverse(self, flm, out=None):
         return self._call("mw_inverse", flm, self._nflm, self._nmap, out)
+
+    def forward_inverse(self, maps, flm, flm_out=None, map_out=None):
+        """Forward of `maps` and inverse of `flm` (independent inputs) sharing one
+        Wigner-Delta recursion; returns (flm_out, map_out)."""
+        for x, n in ((maps, self._nmap), (flm, self._nflm)):
+            if x.dtype != torch.complex128:
+                raise TypeError("expected complex128 tensors")
+            if x.numel() != n:
+                raise ValueError(f"expected {n} elements, got {tuple(x.shape)}")
+        maps, flm = maps.contiguous(), flm.contiguous()
+
+        def make(o, n, like):
+            if o is None:
+                shape = (self.batch, n // self.batch) if self._uniform else (n,)
+                return torch.empty(shape, dtype=torch.complex128, device=like.device)
+            if o.dtype != torch.complex128 or o.numel() != n or not o.is_contiguous():
+                raise ValueError("bad output tensor")
+            return o
+
+        flm_out = make(flm_out, self._nflm, maps)
+        map_out = make(map_out, self._nmap, flm)
+        st = lib().mw_forward_inverse(self._h, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(flm_out.data_ptr()),
+                                      ctypes.c_void_p(flm.data_ptr()), ctypes.c_void_p(map_out.data_ptr()),
+                                      _stream_of(maps))
+        if st != MW_OK:
+            raise MWError(st, "mw_forward_inverse")
+        return flm_out, map_out
 
     def forward_adjoint(self, flm, out=None):
         return self._call("mw_forward_adjoint", flm, self._nflm, self._nmap, out)

@@ -93,9 +93,10 @@ def workload_ragged(n_maps: int = 64):
     return dict(Ls=[int(x) for x in Ls], spins=[int(x) for x in ss], flm=flm)
 
 
-def workload_l2048_b16(n_maps: int = 16, L: int = 2048):
-    """L=2048, B=16: maps 0..7 spin 0 and maps 8..15 spin 2, E|f_lm|^2 = 1/(l+1)^2."""
-    g = rng(4)
+def workload_l2048_b16(n_maps: int = 16, L: int = 2048, seed: int = 4):
+    """L=2048, B=16: maps 0..7 spin 0 and maps 8..15 spin 2, E|f_lm|^2 = 1/(l+1)^2.
+    Another seed gives an independent batch of the same shape."""
+    g = rng(seed)
     spins = [0] * (n_maps // 2) + [2] * (n_maps - n_maps // 2)
     flm = [gaussian_flm(g, L, s, cl_red) for s in spins]
     return dict(L=L, spins=spins, flm=flm)

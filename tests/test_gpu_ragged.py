@@ -89,9 +89,29 @@ def test_graph_replay_matches_direct(mw, prec):
     for _ in range(3):  # capture, then replays
         graphed.inverse(flm, out=out)
     graphed.sync()
+    assert graphed.last_launches == 1  # replayed as one graph launch
     assert torch.equal(a, out)
     b1 = direct.forward(a)
     b2 = torch.empty_like(b1)
     for _ in range(2):
         graphed.forward(a, out=b2)
+    assert graphed.last_launches == 1
     assert torch.equal(b1, b2)
+
+
+def test_graph_replay_on_a_side_stream(mw):
+    L, spins = 64, [0, 1]
+    g = wl.rng(8)
+    flm = torch.from_numpy(np.stack([wl.gaussian_flm(g, L, s, wl.cl_red) for s in spins])).cuda()
+    ref = mw.Plan(L, spins, precision="mixed").inverse(flm)
+    graphed = mw.Plan(L, spins, precision="mixed", graph=True)
+    out = torch.empty_like(ref)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            graphed.inverse(flm, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    assert graphed.last_launches == 1
+    assert torch.equal(out, ref)
