@@ -18,7 +18,7 @@ struct FftDesc {
 // Each group holds at most kMaxGroupMaps maps (larger spin classes are split).
 constexpr int kMaxGroupMaps = 32;
 constexpr int kChunk = 64;         // Delta planes staged per FP64 contraction launch
-constexpr int kTcChunk = 128;      // Delta planes staged per tensor-core contraction launch
+constexpr int kTcChunk = 512;      // Delta planes staged per tensor-core contraction launch (8.7 GB at L=2048)
 constexpr int kTcGroupMaps = 8;    // maps per spin group on both contraction paths (N = 4 x 8)
 
 struct SpinGroup {
@@ -60,7 +60,8 @@ struct mw_plan {
 
   // workspace
   void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
-  double2* d_Gp = nullptr;         // [B][M][L] folded G+_{m,m'} or F+_{m,m'}, m' >= 0
+  double2* d_Gp = nullptr;         // [B][M][L] folded G+_{m,m'} or F+_{m,m'}, m' >= 0; on the mixed path G+
+                                   // as float2 and F+ as float-float (re_hi, re_lo, im_hi, im_lo)
   double* d_S = nullptr;           // FP64 path: [kChunk][LD][LD] staged integer Delta planes (quarter);
                                    // mixed path: [2][LD][LD] ping-pong recursion state
   float* d_S32 = nullptr;          // mixed path: [kTcChunk][LD][LD] FP32 copies of the integer planes

@@ -42,6 +42,19 @@ template <typename T>
 __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
 template <typename T>
 __device__ __forceinline__ C<T> from64(double2 v) { return mkc<T>((T)v.x, (T)v.y); }
+
+// Element idx of the inverse contraction's F+ buffer: FP64 complex on the FP64
+// path; on the mixed path float-float pairs (re_hi, re_lo, im_hi, im_lo) in the
+// same 16 bytes, read as hi + lo in single precision.
+template <typename T>
+__device__ __forceinline__ C<T> load_fplus(const double2* __restrict__ Fp, long long idx) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = reinterpret_cast<const float4*>(Fp)[idx];
+    return mkc<T>(v.x + v.y, v.z + v.w);
+  } else {
+    return from64<T>(Fp[idx]);
+  }
+}
 __device__ __forceinline__ double2 to64(double2 v) { return v; }
 __device__ __forceinline__ double2 to64(float2 v) { return make_double2(v.x, v.y); }
 
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDes
     const int mp = (k <= L - 1) ? k : k - M;  // slot of m' in the length-M DFT
     const int a = mp < 0 ? -mp : mp;
     const int q = ph + ((mp < 0 && ((m + s) & 1)) ? 2 : 0);
-    const C<T> y = mul_ipow<T>(from64<T>(in[a]), q);
+    const C<T> y = mul_ipow<T>(load_fplus<T>(in, a), q);
     // times e^{+i m' pi / M} = conj(phase)
     buf[k] = cmulc<T>(y, phase[mp + L - 1]);
   }
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_adjoint(Dims d
     if (mp == 0x7fffffff) { buf[k] = mkc<T>(0, 0); continue; }
     const int a = mp < 0 ? -mp : mp;
     const int q = ph + ((mp < 0 && ((m + s) & 1)) ? 2 : 0);
-    buf[k] = mul_ipow<T>(from64<T>(in[a]), q);
+    buf[k] = mul_ipow<T>(load_fplus<T>(in, a), q);
   }
   __syncthreads();
   // convolution^H: zero-pad, inverse DFT, times conj(V), DFT; then the theta-DFT^H:
@@ -395,14 +408,19 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse_adjoint(Dims d
 // inherit the cancellation of the alternating sum over the FFT output.
 __global__ void k_pole_forward_adjoint(Dims d, const double2* __restrict__ Gp, const double2* __restrict__ upole,
                                        double2* __restrict__ map, const long long* __restrict__ moff,
-                                       const int* __restrict__ spins) {
+                                       const int* __restrict__ spins, int float_float) {
   __shared__ double2 red[256];
   const int b = blockIdx.x, L = d.L, M = d.M;
   const int s = spin_of(spins, b);
   const double2* w = Gp + ((long long)b * M + (s + L - 1)) * L;
   double sr = 0.0, si = 0.0;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    const double2 x = w[mp], u = upole[mp];
+    double2 x = w[mp];
+    if (float_float) {  // mixed path: (re_hi, re_lo, im_hi, im_lo)
+      const float4 v = reinterpret_cast<const float4*>(w)[mp];
+      x = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+    const double2 u = upole[mp];
     sr += x.x * u.x - x.y * u.y;
     si += x.x * u.y + x.y * u.x;
   }
@@ -571,6 +589,7 @@ cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st) {
   return DISPATCH(p, theta_inverse_adjoint_t, p, st);
 }
 cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st) {
-  k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_moff, p->d_spins);
+  k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_moff, p->d_spins,
+                                                p->prec == MW_PREC_MIXED ? 1 : 0);
   return cudaGetLastError();
 }

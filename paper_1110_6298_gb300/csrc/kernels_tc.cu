@@ -1,6 +1,6 @@
 // kernels_tc.cu -- split-precision Delta contractions on the tensor cores (tcgen05).
 //
-// For one chunk of 128 consecutive l and one |m| = am, the forward sum of
+// For one tile of 128 consecutive l and one |m| = am, the forward sum of
 // Eq. (flm_wig) over m' >= 0 (the +-m' fold is already in G+) is a GEMM
 //   out[l, n] = sum_{m'} A[l, m'] B[n, m'],   A[l, m'] = Delta^l_{m',am} Delta^l_{m',-s}
 // with n running over (map, re/im) for m = +am and, for m = -am, over the same
@@ -56,6 +56,17 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
   const float err = (hi - (s - bb)) + (b - bb);
   hi = s;
   lo += err;
+}
+
+// (h, l) += (bh, bl) in float-float: TwoSum of the high words, then the low
+// words and the rounding error, renormalised (Fast2Sum).
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (bh - bb);
+  const float t = l + bl + e;
+  h = s + t;
+  l = t - (h - s);
 }
 
 // Issue the 4 K steps x 6 split products of one 64-wide K tile into the six
@@ -163,7 +174,7 @@ __device__ __forceinline__ void kernel8(const float* __restrict__ P, int LD, int
 // ---------------------------------------------------------------------------
 // forward: f_lm for l in [l0, l1), both signs of m = +-am, every spin group
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
+__global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
                                                          int l1, const SpinGroup* __restrict__ groups, int ng,
                                                          const float2* __restrict__ Gp,
                                                          const double* __restrict__ nltab,
@@ -175,8 +186,11 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 3 * kATile + 3 * kBTile);
   uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int am = blockIdx.x;
+  const int lt0 = l0 + 128 * blockIdx.y;           // rows l of this block: [lt0, lt1)
+  const int lt1 = min(l1, lt0 + 128);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, half = warp >> 2;
+  if (am >= lt1) return;  // block-uniform: no row l >= |m| here
   if (tid == 0) umma::mbar_init(mbar, 1);
   if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
   sync_all();
@@ -185,62 +199,67 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
   const size_t plane = (size_t)LD * LD;
   uint32_t phase = 0;
   bool ok = true;
-  const int row = quad * 32 + lane;  // TMEM lane = tile row = l - l0
+  const int row = quad * 32 + lane;  // TMEM lane = tile row = l - lt0
   for (int gi = 0; gi < ng; ++gi) {
     const SpinGroup& g = groups[gi];
     const int s = g.s, as = s < 0 ? -s : s, nb = g.nb;
-    const int lstart = max(max(l0, am), as);
+    const int lstart = max(max(lt0, am), as);
     float ahi[16], alo[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
-    if (lstart < l1) {
-      for (int mp0 = 0; mp0 < l1; mp0 += kKTile) {
-        // A: 128 rows x 8 chunks of 8 m'.  Lanes 8q..8q+7 take the 8 rows of
-        // one core matrix (each 8-lane phase of the 16-byte stores fills 128
-        // contiguous bytes: no bank conflicts) and the four lane octets of a
-        // warp take consecutive chunks (128 contiguous bytes of each plane row).
-        for (int task = tid; task < 128 * (kKTile / 8); task += kThreads) {
-          const int r = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
-          const int l = l0 + r, mp = mp0 + 8 * c;
-          float x[8];
-          if (l >= lstart && l < l1 && mp <= l) {
-            kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, x);
+    if (lstart < lt1) {
+      // Thread tid stages A rows r0 + 32k (k < 4) and B row r0 of 8-column chunk
+      // cq: lanes 8q..8q+7 take the 8 rows of one core matrix (each 8-lane
+      // phase of the 16-byte stores fills 128 contiguous bytes: no bank
+      // conflicts) and the four lane octets of a warp take consecutive chunks
+      // (128 contiguous bytes of each plane row).  The next tile's values are
+      // gathered into registers while the current tile's MMAs and drain run.
+      const int r0 = (tid & 7) + 8 * (tid >> 6), cq = (tid >> 3) & 7;
+      float xa[4][8], xb[8];
+      auto gather = [&](int mp0) {
+        const int mp = mp0 + 8 * cq;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int l = lt0 + r0 + 32 * k;
+          if (l >= lstart && l < lt1 && mp <= l) {
+            kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, xa[k]);
           } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = 0.f;
+            for (int i = 0; i < 8; ++i) xa[k][i] = 0.f;
           }
-          store_split8(sA, kATile, umma::tile_off(r, 8 * c, kKTile / 8), x);
         }
-        // B: 32 rows (map, re/im; +am then -am) x 8 chunks, same lane order as A
-        for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
-          const int n = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
-          const int j = n >> 1, mp = mp0 + 8 * c;
-          float x[8];
+        // B row n = r0: (map, re/im) for +am, then the same maps for -am
+        const int n = r0, j = n >> 1;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = 0.f;
-          if (j < 2 * nb) {
-            const bool neg = j >= nb;
-            if (!(neg && am == 0)) {
-              const float2* src = Gp + ((size_t)g.maps[neg ? j - nb : j] * M + (neg ? -am : am) + L - 1) * L;
+        for (int i = 0; i < 8; ++i) xb[i] = 0.f;
+        if (j < 2 * nb) {
+          const bool neg = j >= nb;
+          if (!(neg && am == 0)) {
+            const float2* src = Gp + ((size_t)g.maps[neg ? j - nb : j] * M + (neg ? -am : am) + L - 1) * L;
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                if (mp + i < L) {
-                  const float2 v = src[mp + i];
-                  float y = (n & 1) ? v.y : v.x;
-                  if (neg && ((mp + i) & 1)) y = -y;
-                  x[i] = y;
-                }
+            for (int i = 0; i < 8; ++i) {
+              if (mp + i < L) {
+                const float2 v = src[mp + i];
+                float y = (n & 1) ? v.y : v.x;
+                if (neg && ((mp + i) & 1)) y = -y;
+                xb[i] = y;
               }
             }
           }
-          store_split8(sB, kBTile, umma::tile_off(n, 8 * c, kKTile / 8), x);
         }
+      };
+      gather(0);
+      for (int mp0 = 0; mp0 < lt1; mp0 += kKTile) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) store_split8(sA, kATile, umma::tile_off(r0 + 32 * k, 8 * cq, kKTile / 8), xa[k]);
+        store_split8(sB, kBTile, umma::tile_off(r0, 8 * cq, kKTile / 8), xb);
         umma::fence_proxy_async();
         sync_all();
         if (tid == 0) {
           issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
           umma::commit(mbar);
         }
+        if (mp0 + kKTile < lt1) gather(mp0 + kKTile);
         const bool w = wait_all(mbar, phase);
         phase ^= 1u;
         ok = ok && w;
@@ -249,8 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
       }
     }
     // epilogue: columns 16*half .. +15 = (map j, re/im) for j = 8*half .. 8*half+7
-    const int l = l0 + row;
-    if (l >= am && l < l1) {
+    const int l = lt0 + row;
+    if (l >= am && l < lt1) {
       const double nl = ((s & 1) ? -1.0 : 1.0) * nltab[l];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
@@ -284,14 +303,16 @@ __global__ void __launch_bounds__(kThreads) k_tc_forward(const float* __restrict
 
 // ---------------------------------------------------------------------------
 // inverse: F+_{+-am, m'} += sum_{l in [l0,l1)} N_l Delta^l_{m',am} Delta^l_{m',-s} f_{l,+-am}
-// one block per (am, 128-row tile of m', spin group).  The A operand (rows m',
+// one block per (am, 128-row tile of m', spin group).  F+ is kept across chunks
+// as float-float pairs (about 48 significant bits): no FP64 arithmetic, which
+// runs at 1/64 of the FP32 rate on this part.  The A operand (rows m',
 // K = l) is stored MN-major: each 16-byte core-matrix row holds 8 consecutive m'
 // of one l, exactly the layout of a plane row.
 // ---------------------------------------------------------------------------
 constexpr int kMnSbo = 128;                  // stride between 8-m' groups
 constexpr int kMnLbo = (128 / 8) * 128;      // stride between 8-l groups (2048)
 
-__global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
+__global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
                                                          int l1, const SpinGroup* __restrict__ groups,
                                                          const float2* __restrict__ flmf, double2* __restrict__ Fp,
                                                          int* __restrict__ err) {
@@ -318,48 +339,55 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
   float ahi[16], alo[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) { ahi[j] = 0.f; alo[j] = 0.f; }
-  for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
-    const int lb = l0 + kt * kKTile;
-    // A: 64 l x 16 chunks of 8 m'.  Lanes 8q..8q+7 take 8 consecutive l (one
-    // MN-major core matrix: conflict-free 16-byte stores), the lane octets
-    // consecutive chunks of m'.
-    for (int task = tid; task < kKTile * 16; task += kThreads) {
-      const int k = (task & 7) + 8 * (task >> 7), c = (task >> 3) & 15;
-      const int l = lb + k, mp = mp0 + 8 * c;
-      float x[8];
+  // Thread tid stages A rows k0 + 16q (q < 4; rows are l, columns 8-wide
+  // chunks cA of m') and B row n0 of chunk cB.  Lanes 8q..8q+7 take 8
+  // consecutive l (one MN-major core matrix: conflict-free 16-byte stores), the
+  // lane octets consecutive chunks.  The next tile is gathered into registers
+  // while the current tile's MMAs and drain run.
+  const int k0 = (tid & 7) + 8 * (tid >> 7), cA = (tid >> 3) & 15;
+  const int n0 = (tid & 7) + 8 * (tid >> 6), cB = (tid >> 3) & 7;
+  float xa[4][8], xb[8];
+  auto gather = [&](int lb) {
+    const int mp = mp0 + 8 * cA;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int l = lb + k0 + 16 * q;
       if (l >= lstart && l < l1 && mp <= l && mp < L) {
-        kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, x);
+        kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, xa[q]);
       } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = 0.f;
+        for (int i = 0; i < 8; ++i) xa[q][i] = 0.f;
       }
-      store_split8(sA, kATile, c * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, x);
     }
-    // B: 32 rows (map, re/im) x 8 chunks of 8 l (K-major), lane order as above
-    for (int task = tid; task < kN * (kKTile / 8); task += kThreads) {
-      const int n = (task & 7) + 8 * (task >> 6), c = (task >> 3) & 7;
-      const int j = n >> 1;
-      float x[8];
+    const int j = n0 >> 1;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = 0.f;
-      if (j < 2 * nb) {
-        const bool neg = j >= nb;
-        if (!(neg && am == 0)) {
-          const int b = g.maps[neg ? j - nb : j];
+    for (int i = 0; i < 8; ++i) xb[i] = 0.f;
+    if (j < 2 * nb) {
+      const bool neg = j >= nb;
+      if (!(neg && am == 0)) {
+        const int b = g.maps[neg ? j - nb : j];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int l = lb + 8 * c + i;
-            if (l >= lstart && l < l1) {
-              const float2 f = flmf[(size_t)b * L * L + (size_t)l * l + l + (neg ? -am : am)];  // N_l f_lm
-              float y = (n & 1) ? f.y : f.x;
-              if (neg && (l & 1)) y = -y;
-              x[i] = y;
-            }
+        for (int i = 0; i < 8; ++i) {
+          const int l = lb + 8 * cB + i;
+          if (l >= lstart && l < l1) {
+            const float2 f = flmf[(size_t)b * L * L + (size_t)l * l + l + (neg ? -am : am)];  // N_l f_lm
+            float y = (n0 & 1) ? f.y : f.x;
+            if (neg && (l & 1)) y = -y;
+            xb[i] = y;
           }
         }
       }
-      store_split8(sB, kBTile, umma::tile_off(n, 8 * c, kKTile / 8), x);
     }
+  };
+  gather(l0);
+  for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
+    const int lb = l0 + kt * kKTile;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + 16 * q;
+      store_split8(sA, kATile, cA * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, xa[q]);
+    }
+    store_split8(sB, kBTile, umma::tile_off(n0, 8 * cB, kKTile / 8), xb);
     umma::fence_proxy_async();
     sync_all();
     if (tid == 0) {
@@ -378,6 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
       }
       umma::commit(mbar);
     }
+    if ((kt + 1) * kKTile < l1 - l0) gather(lb + kKTile);
     const bool w = wait_all(mbar, phase);
     phase ^= 1u;
     ok = ok && w;
@@ -395,12 +424,12 @@ __global__ void __launch_bounds__(kThreads) k_tc_inverse(const float* __restrict
       const bool neg = j >= nb;
       if (neg && am == 0) continue;
       const int b = g.maps[neg ? j - nb : j];
-      double2* dst = Fp + ((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp;
-      double re = (double)ahi[2 * jj] + (double)alo[2 * jj], im = (double)ahi[2 * jj + 1] + (double)alo[2 * jj + 1];
-      if (neg && (mp & 1)) { re = -re; im = -im; }
-      double2 cur = *dst;
-      cur.x += re;
-      cur.y += im;
+      float4* dst = reinterpret_cast<float4*>(Fp) + ((size_t)b * M + (neg ? -am : am) + L - 1) * L + mp;
+      float rh = ahi[2 * jj], rl = alo[2 * jj], ih = ahi[2 * jj + 1], il = alo[2 * jj + 1];
+      if (neg && (mp & 1)) { rh = -rh; rl = -rl; ih = -ih; il = -il; }
+      float4 cur = *dst;
+      ff_add(cur.x, cur.y, rh, rl);
+      ff_add(cur.z, cur.w, ih, il);
       *dst = cur;
     }
   }
@@ -432,7 +461,8 @@ cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t
 cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
-  k_tc_forward<<<l1, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
+  const dim3 grid(l1, (l1 - l0 + 127) / 128);
+  k_tc_forward<<<grid, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
                                        reinterpret_cast<const float2*>(p->d_Gp), p->d_nl, flm, p->d_foff, p->d_err);
   return cudaGetLastError();
 }

@@ -256,7 +256,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   } else {
     const size_t plane = (size_t)p->LD * p->LD;
     alloc((void**)&p->d_S, sizeof(double) * (dbl ? (size_t)kChunk : 2) * plane);
-    if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)kTcChunk * plane);
+    if (!dbl) alloc((void**)&p->d_S32, sizeof(float) * (size_t)(L < kTcChunk ? L : kTcChunk) * plane);
     alloc((void**)&p->d_err, sizeof(int));
     if (e == cudaSuccess) chk(cudaMemset(p->d_err, 0, sizeof(int)));
     {
