@@ -98,6 +98,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_max(x, device=None):
+    """Max of x over the ranks of the default process group (x itself when
+    there is none): the job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_value(world, batch, steps, seconds):
+    """Transforms/s of the whole job: each of the `world` ranks runs `steps`
+    steps of 2 * batch transforms (forward + inverse) in `seconds` (max over
+    ranks).  Weak scaling: the per-rank work does not depend on world."""
+    return world * 2 * batch * steps / seconds
+
+
 def contraction_units(L, spins):
     """(l, m, m' >= 0, map) real-kernel x complex multiply-accumulates of one
     direction's Delta contraction (4 flops each)."""
@@ -169,18 +194,10 @@ def run_ours(args, rank, world, local_rank):
     # forward(inverse(flm2)) must give flm2 back
     err = float((flm_out - flm2).abs().max().item() / flm2.abs().max().item())
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = rank_barrier
 
     def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            x = float(t.item())
-        return x
+        return rank_max(x, dev)
 
     clocks = ClockSampler(local_rank)
     plan.set_timing(True)
@@ -200,7 +217,7 @@ def run_ours(args, rank, world, local_rank):
     ms = max_over_ranks(e0.elapsed_time(e1))
     stages = plan.stage_times(reset=True)
     plan.set_timing(False)
-    value = world * 2 * B * args.steps / (ms / 1e3)
+    value = whole_job_value(world, B, args.steps, ms / 1e3)
 
     # context: the dependent round trip (inverse, then forward of its output),
     # which cannot share a sweep: two recursions per step
@@ -233,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
         plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
     torch.cuda.synchronize(dev)
     t_e2e = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * 2 * B * e2e_steps / t_e2e
+    e2e_value = whole_job_value(world, B, e2e_steps, t_e2e)
     bytes_flm = B * L * L * 16
     bytes_map = B * nmw * 16
 
@@ -280,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
                    "spins": spins, "precision": args.precision, "l2_flush": "inputs larger than L2",
                    "parallelism": f"replicas x{world}"},
         "roundtrip_rel_err": err,
-        "roundtrip": {"value": world * 2 * B * args.steps / (rt_ms / 1e3), "unit": "transforms/s",
+        "roundtrip": {"value": whole_job_value(world, B, args.steps, rt_ms / 1e3), "unit": "transforms/s",
                       "ms_per_step": rt_ms / args.steps, "rel_err": rt_err,
                       "what": "inverse then forward of its output (two recursions per step)"},
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
