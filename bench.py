@@ -246,8 +246,11 @@ def run_ours(args, rank, world, local_rank):
     plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
     barrier()
     t0 = time.perf_counter()
+    e2e_each = []
     for _ in range(e2e_steps):
+        ts = time.perf_counter()
         plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
+        e2e_each.append(1e3 * (time.perf_counter() - ts))
     torch.cuda.synchronize(dev)
     t_e2e = max_over_ranks(time.perf_counter() - t0)
     e2e_value = whole_job_value(world, B, e2e_steps, t_e2e)
@@ -301,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": rt_ms / args.steps, "rel_err": rt_err,
                       "what": "inverse then forward of its output (two recursions per step)"},
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
-                "d2h_bytes_per_step": bytes_map + bytes_flm},
+                "d2h_bytes_per_step": bytes_map + bytes_flm, "ms_each_step": e2e_each},
         "gpu_launches": launches_per_step * args.steps,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "roofline": roof,
