@@ -54,8 +54,8 @@ __device__ __forceinline__ float to_f32_int(double v) {
 // ---------------------------------------------------------------------------
 // Persistent Risbo sweep over the planes l in [l_begin, l_end) of one chunk.
 //
-// One cooperative launch per chunk; a grid-wide barrier (bounded spin) separates
-// consecutive l.  Each l is one pass over 32 x 32 tiles of the lower triangle
+// One cooperative launch per chunk of planes.  Each l is one pass over 32 x 32
+// tiles of the lower triangle
 // b <= a of the new quarter plane (the transpose symmetry supplies the rest):
 // a tile stages the previous integer plane Delta^{l-1} on rows/columns
 // a0-1 .. a0+32 in shared memory, computes the half-integer plane d^{l-1/2} on
@@ -63,7 +63,7 @@ __device__ __forceinline__ float to_f32_int(double v) {
 // from the gather formula) and from it the integer plane Delta^l on the tile.
 // Recomputing the 33 x 33 half plane per tile costs 6% more FP64 work than a
 // global half step but saves a grid barrier and the half plane's memory
-// traffic per l.  Per element the stencil costs 6 FP64 instructions: with the
+// traffic per l.  Per element the stencil costs 5 FP64 instructions: with the
 // column factors cn = sqrt(j'-nu)/(2 sqrt2 j'), cp = sqrt(j'+nu)/(2 sqrt2 j')
 // kept in shared memory,
 //   e = cn (sqrt(j'-mu) d_{+,+} - sqrt(j'+mu) d_{-,+}) + cp (sqrt(j'-mu) d_{+,-} + sqrt(j'+mu) d_{-,-}).
@@ -168,9 +168,23 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
       }
       __syncthreads();
       if (!s_ok) return;
-      for (int idx = tid; idx < (kRT + 2) * (kRT + 2); idx += kRThreads) {
-        const int r = idx / (kRT + 2), c = idx % (kRT + 2);
-        dh[r][c] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+      {  // all of a thread's halo loads are issued before any is stored
+        constexpr int kLoads = ((kRT + 2) * (kRT + 2) + kRThreads - 1) / kRThreads;  // 5
+        double v[kLoads];
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+          const int idx = tid + q * kRThreads;
+          v[q] = 0.0;
+          if (idx < (kRT + 2) * (kRT + 2)) {
+            const int r = idx / (kRT + 2), c = idx % (kRT + 2);
+            v[q] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+          const int idx = tid + q * kRThreads;
+          if (idx < (kRT + 2) * (kRT + 2)) dh[idx / (kRT + 2)][idx % (kRT + 2)] = v[q];
+        }
       }
       if (tid < kRT + 1) {  // half-plane column factors, columns k = b0-1 .. b0+31 (nu = k + 1/2)
         const int nu2 = 2 * (b0 - 1 + tid) + 1;
