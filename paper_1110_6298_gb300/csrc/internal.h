@@ -53,6 +53,7 @@ struct mw_plan {
   void* d_phase = nullptr;         // e^{-i pi m' / M}, m' = -(L-1)..L-1 (index m'+L-1)
   void* d_V = nullptr;             // DFT_N of the reflected weights, pre-scaled by 1/(N M)
   double* d_sqrt = nullptr;        // sqrt(k), k = 0..2L+2
+  double* d_rsqrt = nullptr;       // 1/sqrt(k), k = 1..2L+2 (entry 0 unused, 0)
   double2* d_upole = nullptr;      // u(m') + u(-m') (m' > 0), u(0): pole row of the forward adjoint
   double* d_rscale = nullptr;      // 1 / (sqrt2 * two_jp) for the Risbo half step to plane two_jp / 2
   double* d_nl = nullptr;          // sqrt((2l+1)/(4 pi)), l < L

@@ -83,6 +83,7 @@ struct RisboArgs {
   int full64;         // write transposed tiles into the FP64 integer plane
   int LD;
   const double* sq;      // sqrt(k)
+  const double* rsq;     // 1/sqrt(k), k >= 1
   const double* rscale;  // 1 / (sqrt2 two_jp)
   int* prog;          // per-tile progress: last plane l published
   int* err;
@@ -129,15 +130,27 @@ __global__ void k_prog_init(int* prog, int n, int value) {
 // that exceeds its poll limit records the timeout and the block leaves.  A
 // block that overwrites plane l-2 (two-plane ping-pong) does so only after all
 // readers of that region -- its neighbours at step l-1 -- have finished.
-__global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
-  __shared__ double dh[kRT + 2][kRT + 3];   // Delta^{l-1} on rows/cols a0-1 .. a0+32
-  __shared__ double hh[kRT + 1][kRT + 1];   // d^{l-1/2} on rows/cols a0-1 .. a0+31 (odd row stride)
-  __shared__ double tr[kRT][kRT + 1];
-  __shared__ double colf[4][kRT + 1];       // cn, cp of the half plane (33 cols) and of the integer plane (32)
-  __shared__ int s_ok;
+// Shared memory of one block: kPair tiles of one step are processed together
+// (tiles t and t + G are far apart, so neither waits for the other).  One tile
+// per pass measured as fast as two, with half the shared memory.
+constexpr int kPair = 1;
+struct RisboSmem {
+  double dh[kPair][kRT + 2][kRT + 3];  // Delta^{l-1} on rows/cols a0-1 .. a0+32
+  double hh[kPair][kRT + 1][kRT + 1];  // d^{l-1/2} on rows/cols a0-1 .. a0+31
+  double tr[kPair][kRT][kRT + 1];      // Delta^l on the tile
+  double colf[kPair][4][kRT + 1];      // cn, cp of the half plane (33 cols) and of the integer plane (32)
+  double rowf[kPair][4][kRT + 1];      // sqrt(j'-mu), sqrt(j'+mu) of the half-plane rows (33) and integer rows (32)
+  int ok;
+};
+constexpr int kRisboSmem = (int)sizeof(RisboSmem);
+
+__global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
+  extern __shared__ __align__(16) unsigned char risbo_smem[];
+  RisboSmem& sm = *reinterpret_cast<RisboSmem*>(risbo_smem);
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int LD = A.LD;
   const size_t plane = (size_t)LD * LD;
+  const int G = gridDim.x;
   for (int l = l_begin; l < l_end; ++l) {
     const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
     const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
@@ -148,134 +161,231 @@ __global__ void __launch_bounds__(kRThreads) k_risbo_sweep(RisboArgs A, int l_be
     const int T = (nnew + kRT - 1) / kRT;       // tile rows of plane l
     const int Tp = (l + kRT - 1) / kRT;         // tile rows of plane l-1 (size l)
     const int ntiles = T * (T + 1) / 2;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-      while (I * (I + 1) / 2 > t) --I;
-      while ((I + 1) * (I + 2) / 2 <= t) ++I;
-      const int J = t - I * (I + 1) / 2;
-      const int a0 = I * kRT, b0 = J * kRT;
-      if (tid < 32) {  // lanes 0..8 each wait for one neighbour, concurrently
+    for (int tb = blockIdx.x; tb < ntiles; tb += kPair * G) {
+      int tt[kPair], II[kPair], JJ[kPair];
+      int np = 0;
+#pragma unroll
+      for (int k = 0; k < kPair; ++k) {
+        const int t = tb + k * G;
+        tt[k] = t;
+        II[k] = JJ[k] = 0;
+        if (t < ntiles) {
+          int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+          while (I * (I + 1) / 2 > t) --I;
+          while ((I + 1) * (I + 2) / 2 <= t) ++I;
+          II[k] = I;
+          JJ[k] = t - I * (I + 1) / 2;
+          np = k + 1;
+        }
+      }
+      if (tid < 32) {  // lanes 16k + q (q < 9) wait for neighbour q of tile k, concurrently
         int ok = 1;
-        if (l > l_begin && tx < 9) {
-          const int Ii = I + tx / 3 - 1, Jj = J + tx % 3 - 1;
+        const int k = tx >> 4, q = tx & 15;
+        if (l > l_begin && k < np && q < 9) {
+          const int Ii = II[k] + q / 3 - 1, Jj = JJ[k] + q % 3 - 1;
           if (Ii >= 0 && Jj >= 0 && Ii < Tp && Jj < Tp) {  // part of plane l-1
             const int hi = Ii > Jj ? Ii : Jj, lo = Ii > Jj ? Jj : Ii;
             if (!wait_tile(A.prog, tile_index(hi, lo), l - 1)) { ok = 0; atomicOr(A.err, 2); }
           }
         }
         ok = __all_sync(0xffffffffu, ok);
-        if (tx == 0) s_ok = ok && !*(volatile int*)A.err;
+        if (tx == 0) sm.ok = ok && !*(volatile int*)A.err;
+      } else {
+        // meanwhile the other warps stage the row and column factors, which do
+        // not depend on the neighbours, so that no FP64 phase starts with a
+        // global load: per tile 33 + 32 rows and 33 + 32 columns
+#pragma unroll
+        for (int k = 0; k < kPair; ++k) {
+          if (k >= np) continue;
+          const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
+          for (int y = tid - 32; y < 2 * (2 * kRT + 1); y += kRThreads - 32) {
+            if (y <= kRT) {  // half-plane row i = a0-1+y (mu = i + 1/2)
+              const int i = a0 - 1 + y, mu2 = 2 * i + 1;
+              const bool in = i < nh;
+              sm.rowf[k][0][y] = in ? A.sq[(th - mu2) / 2] : 0.0;
+              sm.rowf[k][1][y] = in ? A.sq[(th + mu2) / 2] : 0.0;
+            } else if (y < 2 * kRT + 1) {  // integer-plane row a = a0 + r
+              const int r = y - (kRT + 1), a = a0 + r;
+              const bool in = a < nnew;
+              sm.rowf[k][2][r] = in ? A.sq[(ti - 2 * a) / 2] : 0.0;
+              sm.rowf[k][3][r] = in ? A.sq[(ti + 2 * a) / 2] : 0.0;
+            } else if (y < 3 * kRT + 2) {  // half-plane column k = b0-1+c (nu = k + 1/2)
+              const int c = y - (2 * kRT + 1);
+              const int nu2 = 2 * (b0 - 1 + c) + 1;
+              const bool in = (b0 - 1 + c) < nh;
+              if (l == 1) {  // cn, cp themselves
+                sm.colf[k][0][c] = in ? sch * A.sq[(th - nu2) / 2] : 0.0;
+                sm.colf[k][1][c] = in ? sch * A.sq[(th + nu2) / 2] : 0.0;
+              } else {  // cn / cp (cp = sch sqrt(l + k) > 0 inside the plane)
+                sm.colf[k][0][c] = in ? A.sq[(th - nu2) / 2] * A.rsq[(th + nu2) / 2] : 0.0;
+                sm.colf[k][1][c] = 0.0;
+              }
+            } else {  // integer-plane column b = b0 + c
+              const int c = y - (3 * kRT + 2), bcol = b0 + c;
+              const bool in = bcol < nnew;
+              double f2 = in ? sci * A.sq[(ti - 2 * bcol) / 2] : 0.0;
+              double f3 = in ? sci * A.sq[(ti + 2 * bcol) / 2] : 0.0;
+              if (l > 1) {  // absorb the scales cp of half-plane columns c and c+1
+                const int kc = b0 - 1 + c;    // half-plane column of hh column c
+                f3 *= (kc < nh) ? sch * A.sq[l + kc] : 0.0;
+                f2 *= (kc + 1 < nh) ? sch * A.sq[l + kc + 1] : 0.0;
+              }
+              sm.colf[k][2][c] = f2;
+              sm.colf[k][3][c] = f3;
+            }
+          }
+        }
       }
       __syncthreads();
-      if (!s_ok) return;
-      {  // all of a thread's halo loads are issued before any is stored
+      if (!sm.ok) return;
+      {  // all of a thread's halo loads (both tiles) are issued before any is stored
         constexpr int kLoads = ((kRT + 2) * (kRT + 2) + kRThreads - 1) / kRThreads;  // 5
-        double v[kLoads];
+        double v[kPair][kLoads];
 #pragma unroll
-        for (int q = 0; q < kLoads; ++q) {
-          const int idx = tid + q * kRThreads;
-          v[q] = 0.0;
-          if (idx < (kRT + 2) * (kRT + 2)) {
-            const int r = idx / (kRT + 2), c = idx % (kRT + 2);
-            v[q] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+        for (int k = 0; k < kPair; ++k) {
+          const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
+#pragma unroll
+          for (int q = 0; q < kLoads; ++q) {
+            const int idx = tid + q * kRThreads;
+            v[k][q] = 0.0;
+            if (k < np && idx < (kRT + 2) * (kRT + 2)) {
+              const int r = idx / (kRT + 2), c = idx % (kRT + 2);
+              v[k][q] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+            }
           }
         }
 #pragma unroll
-        for (int q = 0; q < kLoads; ++q) {
-          const int idx = tid + q * kRThreads;
-          if (idx < (kRT + 2) * (kRT + 2)) dh[idx / (kRT + 2)][idx % (kRT + 2)] = v[q];
+        for (int k = 0; k < kPair; ++k) {
+#pragma unroll
+          for (int q = 0; q < kLoads; ++q) {
+            const int idx = tid + q * kRThreads;
+            if (k < np && idx < (kRT + 2) * (kRT + 2)) sm.dh[k][idx / (kRT + 2)][idx % (kRT + 2)] = v[k][q];
+          }
         }
-      }
-      if (tid < kRT + 1) {  // half-plane column factors, columns k = b0-1 .. b0+31 (nu = k + 1/2)
-        const int nu2 = 2 * (b0 - 1 + tid) + 1;
-        const bool in = (b0 - 1 + tid) < nh;
-        colf[0][tid] = in ? sch * A.sq[(th - nu2) / 2] : 0.0;
-        colf[1][tid] = in ? sch * A.sq[(th + nu2) / 2] : 0.0;
-      } else if (tid >= 64 && tid < 64 + kRT) {  // integer-plane column factors, b = b0 .. b0+31
-        const int b = b0 + tid - 64;
-        const bool in = b < nnew;
-        colf[2][tid - 64] = in ? sci * A.sq[(ti - 2 * b) / 2] : 0.0;
-        colf[3][tid - 64] = in ? sci * A.sq[(ti + 2 * b) / 2] : 0.0;
       }
       __syncthreads();
       // half plane on (i, k) = (a0-1+r, b0-1+c), r, c < 33; old indices i+1 and i.
       // Row segments: the product sqrt(j'-mu) d_{+,jp} of column c is the
       // sqrt(j'-mu) d_{+,jm} of column c+1, so it is carried along (5 FP64
-      // instructions per element).
-      for (int task = tid; task < (kRT + 1) * 7; task += kRThreads) {
-        const int r = task % (kRT + 1), seg = task / (kRT + 1);
+      // instructions per element).  Thread tid < 231 takes the same segment of
+      // each tile of the pair.
+      if (tid < (kRT + 1) * 7) {
+        const int r = tid % (kRT + 1), seg = tid / (kRT + 1);
         const int c0 = seg * 5, c1 = min(c0 + 5, kRT + 1);  // six segments of 5 columns, one of 3
-        const int i = a0 - 1 + r;
-        if (i >= nh) {
-          for (int c = c0; c < c1; ++c) hh[r][c] = 0.0;
-          continue;
-        }
-        const int mu2 = 2 * i + 1;
-        const double cmm = A.sq[(th - mu2) / 2], cpm = A.sq[(th + mu2) / 2];
-        double pprev = cmm * dh[r + 1][c0];
-        for (int c = c0; c < c1; ++c) {
-          const double p = cmm * dh[r + 1][c + 1];
-          const double t1 = fma(-cpm, dh[r][c + 1], p);
-          const double t2 = fma(cpm, dh[r][c], pprev);
-          hh[r][c] = (b0 - 1 + c < nh) ? fma(colf[1][c], t2, colf[0][c] * t1) : 0.0;
-          pprev = p;
+#pragma unroll
+        for (int k = 0; k < kPair; ++k) {
+          if (k >= np) continue;
+          const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
+          const int i = a0 - 1 + r;
+          if (i >= nh) {
+            for (int c = c0; c < c1; ++c) sm.hh[k][r][c] = 0.0;
+            continue;
+          }
+          const double cmm = sm.rowf[k][0][r], cpm = sm.rowf[k][1][r];
+          double pprev = cmm * sm.dh[k][r + 1][c0];
+          if (l > 1) {
+            // hh holds the half plane divided by its column factor cp (which the
+            // integer step's column factors carry instead): 4 FP64 instructions
+            // per element.  Columns outside the plane have scale 0 there.
+            for (int c = c0; c < c1; ++c) {
+              const double p = cmm * sm.dh[k][r + 1][c + 1];
+              const double t1 = fma(-cpm, sm.dh[k][r][c + 1], p);
+              const double t2 = fma(cpm, sm.dh[k][r][c], pprev);
+              sm.hh[k][r][c] = fma(sm.colf[k][0][c], t1, t2);
+              pprev = p;
+            }
+          } else {
+            for (int c = c0; c < c1; ++c) {
+              const double p = cmm * sm.dh[k][r + 1][c + 1];
+              const double t1 = fma(-cpm, sm.dh[k][r][c + 1], p);
+              const double t2 = fma(cpm, sm.dh[k][r][c], pprev);
+              sm.hh[k][r][c] = (b0 - 1 + c < nh) ? fma(sm.colf[k][1][c], t2, sm.colf[k][0][c] * t1) : 0.0;
+              pprev = p;
+            }
+          }
         }
       }
       __syncthreads();
-      // integer plane on the tile into shared memory (half-plane indices a and a-1
-      // -> hh rows r+1 and r; row segments of 4 columns carry the shared product),
-      // then coalesced stores of the tile and, where needed, of its transpose
-      const bool need_tr = (J < I) && (st || A.full64);
+      // integer plane on each tile into shared memory (half-plane indices a and
+      // a-1 -> hh rows r+1 and r; row segments of 4 columns carry the shared
+      // product), then coalesced stores of the tile and, where needed, of its
+      // transpose
       {
         const int r = tid & 31, seg = tid >> 5;  // 32 rows x 8 segments of 4 columns
-        const int a = a0 + r, c0 = seg * 4;
-        if (a < nnew) {
-          const double cmm = A.sq[(ti - 2 * a) / 2], cpm = A.sq[(ti + 2 * a) / 2];
-          double pprev = cmm * hh[r + 1][c0];
+        const int c0 = seg * 4;
 #pragma unroll
-          for (int c = c0; c < c0 + 4; ++c) {
-            const double p = cmm * hh[r + 1][c + 1];
-            const double t1 = fma(-cpm, hh[r][c + 1], p);
-            const double t2 = fma(cpm, hh[r][c], pprev);
-            pprev = p;
-            tr[r][c] = fma(colf[3][c], t2, colf[2][c] * t1);
+        for (int k = 0; k < kPair; ++k) {
+          if (k >= np) continue;
+          const int a = II[k] * kRT + r;
+          if (a < nnew) {
+            const double cmm = sm.rowf[k][2][r], cpm = sm.rowf[k][3][r];
+            double pprev = cmm * sm.hh[k][r + 1][c0];
+#pragma unroll
+            for (int c = c0; c < c0 + 4; ++c) {
+              const double p = cmm * sm.hh[k][r + 1][c + 1];
+              const double t1 = fma(-cpm, sm.hh[k][r][c + 1], p);
+              const double t2 = fma(cpm, sm.hh[k][r][c], pprev);
+              pprev = p;
+              sm.tr[k][r][c] = fma(sm.colf[k][3][c], t2, sm.colf[k][2][c] * t1);
+            }
+          } else {
+#pragma unroll
+            for (int c = c0; c < c0 + 4; ++c) sm.tr[k][r][c] = 0.0;
           }
-        } else {
-#pragma unroll
-          for (int c = c0; c < c0 + 4; ++c) tr[r][c] = 0.0;
         }
       }
       __syncthreads();
+      // the FP64 state of the tiles (lower triangle), which the neighbours read
+      // at the next step, is written and published first; the FP32 staging
+      // copy and the transposed halves, read only by later kernels, follow
+      // after the publication so that the fence does not wait for them
 #pragma unroll
-      for (int q = 0; q < kRT / 8; ++q) {
-        const int r = ty + 8 * q;
-        const int a = a0 + r, b = b0 + tx;
-        if (a < nnew && b < nnew) {
-          const double v = tr[r][tx];
-          e[(size_t)a * LD + b] = v;
-          if (st) st[(size_t)a * LD + b] = to_f32_int(v);
-        }
-      }
-      if (need_tr) {
+      for (int k = 0; k < kPair; ++k) {
+        if (k >= np) continue;
+        const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
 #pragma unroll
         for (int q = 0; q < kRT / 8; ++q) {
-          const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
-          if (aa < nnew && bb < nnew) {
-            const double v = flip_sign(tr[tx][ty + 8 * q], aa - bb);
-            if (A.full64) e[(size_t)bb * LD + aa] = v;
-            if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
-          }
+          const int r = ty + 8 * q;
+          const int a = a0 + r, bcol = b0 + tx;
+          if (a < nnew && bcol < nnew) e[(size_t)a * LD + bcol] = sm.tr[k][r][tx];
         }
       }
-      __syncthreads();  // all writes of the tile issued
+      __syncthreads();  // all FP64 writes of the tiles issued
       if (tid == 0) {
         __threadfence();
-        asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(A.prog + t), "r"(l) : "memory");
+#pragma unroll
+        for (int k = 0; k < kPair; ++k)
+          if (k < np) asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(A.prog + tt[k]), "r"(l) : "memory");
+      }
+#pragma unroll
+      for (int k = 0; k < kPair; ++k) {
+        if (k >= np) continue;
+        const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
+        if (st) {
+#pragma unroll
+          for (int q = 0; q < kRT / 8; ++q) {
+            const int r = ty + 8 * q;
+            const int a = a0 + r, bcol = b0 + tx;
+            if (a < nnew && bcol < nnew) st[(size_t)a * LD + bcol] = to_f32_int(sm.tr[k][r][tx]);
+          }
+        }
+        if ((JJ[k] < II[k]) && (st || A.full64)) {
+#pragma unroll
+          for (int q = 0; q < kRT / 8; ++q) {
+            const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
+            if (aa < nnew && bb < nnew) {
+              const double v = flip_sign(sm.tr[k][tx][ty + 8 * q], aa - bb);
+              if (A.full64) e[(size_t)bb * LD + aa] = v;
+              if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
+            }
+          }
+        }
       }
     }
   }
 }
 
+// Delta^0 = [1] (and its FP32 copy)
 __global__ void k_plane_init(double* S, float* S32) {
   S[0] = 1.0;
   if (S32) S32[0] = 1.0f;
@@ -294,10 +404,11 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
   if (e != cudaSuccess) return e;
   RisboArgs a;
   a.S = S; a.nslot = nslot; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
-  a.sq = p->d_sqrt; a.rscale = p->d_rscale; a.prog = p->d_prog; a.err = p->d_err;
+  a.sq = p->d_sqrt; a.rsq = p->d_rsqrt; a.rscale = p->d_rscale; a.prog = p->d_prog; a.err = p->d_err;
   void* args[] = {&a, &lb, &le};
-  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args, 0, st);
-  if (nd) *nd += 1;
+  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args,
+                                  (size_t)kRisboSmem, st);
+  if (nd) *nd += 2;  // the progress reset and the sweep
   return e;
 }
 
@@ -361,7 +472,8 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
 // limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 4, the fastest measured).
 int risbo_blocks_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, 0) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_risbo_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kRisboSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, kRisboSmem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }

@@ -68,7 +68,7 @@ void free_plan(mw_plan* p) {
   for (mw_plan* c : p->subs) free_plan(c);
   for (mw_plan* c : p->twins) free_plan(c);
   if (p->shared_sweep) { p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; }
-  void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_upole,
+  void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_rsqrt, p->d_upole,
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff};
@@ -196,6 +196,10 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     for (size_t k = 0; k < sq.size(); ++k) sq[k] = std::sqrt((double)k);
     alloc((void**)&p->d_sqrt, sizeof(double) * sq.size());
     if (e == cudaSuccess) chk(cudaMemcpy(p->d_sqrt, sq.data(), sizeof(double) * sq.size(), cudaMemcpyHostToDevice));
+    std::vector<double> rq(sq.size(), 0.0);
+    for (size_t k = 1; k < rq.size(); ++k) rq[k] = 1.0 / std::sqrt((double)k);
+    alloc((void**)&p->d_rsqrt, sizeof(double) * rq.size());
+    if (e == cudaSuccess) chk(cudaMemcpy(p->d_rsqrt, rq.data(), sizeof(double) * rq.size(), cudaMemcpyHostToDevice));
   }
   if (!sweep_only) {  // u(m') = sum_{|m''| <= L-1} (-1)^{m''} conj(w(m''-m')); folded u(m') + u(-m') for m' > 0
     auto u = [&](int mp, double* ur, double* ui) {
