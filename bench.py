@@ -1,17 +1,15 @@
 """Benchmark: MW forward + inverse transforms/s at L = 2048, 16 maps (8 spin 0,
 8 spin 2), complex Gaussian f_lm with E|f_lm|^2 = 1/(l+1)^2.
 
-One step = the forward transform of B maps and the inverse transform of B
-independent f_lm sets in one fused call (mw_forward_inverse), whose two Wigner
-sums share one Delta recursion: 2B transforms.  The maps are band-limited
-(the inverse of a second seeded f_lm batch, made before timing), so the
-forward half's output is checked against that batch.  The dependent round
-trip (inverse, then forward of its result; two recursions) is timed too and
-reported under "roundtrip".  Inputs (1.1 GB of f_lm, 2.1 GB of maps) are
-larger than L2, so no flush is needed between steps.  value: device-timed
-(CUDA events on the stream) with inputs resident in HBM.  e2e: the same fused
-step through the C ABI with pinned host buffers, host<->device copies inside
-the timed region.  The roofline entry
+One step = the paper's round trip (Sec. V-D): the inverse transform of the
+batch followed by the forward transform of its result, 2B transforms, each
+call replayed as one captured CUDA graph.  Inputs (1.1 GB of f_lm, 2.1 GB of
+maps) are larger than L2, so no flush is needed between steps.  value:
+device-timed (CUDA events on the stream) with inputs resident in HBM.  Also
+reported: separate forward and inverse rates, the fused forward + inverse of
+independent batches that share one Delta recursion (mw_forward_inverse), and
+e2e: the round trip through the C ABI with pinned host buffers, host<->device
+copies inside the timed region.  The roofline entry
 describes the dominant stage, timed live with the library's per-stage events.
 
 --impl reference runs the FP64 CPU oracle (the only baseline this project has)
@@ -165,9 +163,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 or world == 1:
         lib_build.build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    rank_barrier()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = wl.workload_l2048_b16(L=args.L)
@@ -175,103 +171,114 @@ def run_ours(args, rank, world, local_rank):
     B = len(spins)
     nmw = mw.map_size(L)
     flm_h = torch.from_numpy(np.stack(w["flm"]))
-    flm = flm_h.to(dev)                      # input of the inverse half
-    flm2 = torch.from_numpy(np.stack(wl.workload_l2048_b16(L=args.L, seed=14)["flm"])).to(dev)
-    plan = mw.Plan(L, spins, precision=args.precision)
-    maps_in = plan.inverse(flm2)             # input of the forward half: band-limited maps (set-up, untimed)
-    flm_out = torch.empty_like(flm)
-    maps_out = torch.empty((B, nmw), dtype=torch.complex128, device=dev)
+    flm = flm_h.to(dev)
+    # whole calls are captured as CUDA graphs on first use and replayed
+    plan = mw.Plan(L, spins, precision=args.precision, graph=True)
+    maps = torch.empty((B, nmw), dtype=torch.complex128, device=dev)
+    out = torch.empty_like(flm)
     stream = torch.cuda.current_stream(dev)
+    K = args.steps
 
-    def step():
-        plan.forward_inverse(maps_in, flm, flm_out, maps_out)
+    def roundtrip():
+        plan.inverse(flm, out=maps)
+        plan.forward(maps, out=out)
 
-    launches_per_step = 0
+    def timed(fn, n):
+        """n calls of fn bracketed by barriers and syncs; CUDA events on the
+        call stream around each; returns (total ms max over ranks, per-call ms)."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        rank_barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(n):
+            ev[i].record(stream)
+            fn()
+        ev[n].record(stream)
+        torch.cuda.synchronize(dev)
+        rank_barrier()
+        each = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+        return rank_max(ev[0].elapsed_time(ev[n]), dev), each
+
     for _ in range(args.warmup):
-        step()
-        launches_per_step = plan.last_launches
+        roundtrip()
     torch.cuda.synchronize(dev)
-    # forward(inverse(flm2)) must give flm2 back
-    err = float((flm_out - flm2).abs().max().item() / flm2.abs().max().item())
+    plan.sync()
+    err = float((out - flm).abs().max().item() / flm.abs().max().item())
 
-    barrier = rank_barrier
-
-    def max_over_ranks(x):
-        return rank_max(x, dev)
-
+    # the timed round trips (graph replays), clocks sampled meanwhile
     clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms, each = timed(roundtrip, K)
+    ck = clocks.stop()
+    value = whole_job_value(world, B, K, ms / 1e3)
+
+    # per-stage breakdown and kernel count: the same round trip run directly
+    # (per-stage CUDA events on the call stream; graphs are not used meanwhile)
     plan.set_timing(True)
     plan.stage_times(reset=True)
-    barrier()
+    n_bd = 2
+    launches_per_step = 0
+    for _ in range(n_bd):
+        plan.inverse(flm, out=maps)
+        n_inv = plan.last_launches
+        plan.forward(maps, out=out)
+        launches_per_step = n_inv + plan.last_launches
     torch.cuda.synchronize(dev)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    ck = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    stages = plan.stage_times(reset=True)
+    stages = {k: v[0] / n_bd for k, v in plan.stage_times(reset=True).items()}
     plan.set_timing(False)
-    value = whole_job_value(world, B, args.steps, ms / 1e3)
 
-    # context: the dependent round trip (inverse, then forward of its output),
-    # which cannot share a sweep: two recursions per step
-    rt_maps = torch.empty_like(maps_out)
-    rt_out = torch.empty_like(flm)
-    plan.inverse(flm, out=rt_maps)
-    plan.forward(rt_maps, out=rt_out)
-    barrier()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.inverse(flm, out=rt_maps)
-        plan.forward(rt_maps, out=rt_out)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    rt_ms = max_over_ranks(e0.elapsed_time(e1))
-    rt_err = float((rt_out - flm).abs().max().item() / flm.abs().max().item())
-    del rt_maps, rt_out
+    # separate forward and inverse rates
+    inv_ms, _ = timed(lambda: plan.inverse(flm, out=maps), K)
+    fwd_ms, _ = timed(lambda: plan.forward(maps, out=out), K)
 
-    # end to end: pinned host buffers through the C ABI, copies inside the timed region
-    maps_pin = maps_in.cpu().pin_memory()
+    # fused forward + inverse of independent batches (one shared recursion)
+    flm2 = torch.from_numpy(np.stack(wl.workload_l2048_b16(L=args.L, seed=14)["flm"])).to(dev)
+    maps_in = plan.inverse(flm2)
+    fu_flm, fu_map = torch.empty_like(flm), torch.empty_like(maps)
+    plan.forward_inverse(maps_in, flm, fu_flm, fu_map)
+    fu_ms, _ = timed(lambda: plan.forward_inverse(maps_in, flm, fu_flm, fu_map), K)
+    fu_err = float((fu_flm - flm2).abs().max().item() / flm2.abs().max().item())
+    del flm2, maps_in, fu_flm, fu_map
+
+    # end to end: the round trip through the C ABI with pinned host buffers,
+    # host<->device copies inside the timed region
     flm_pin = flm_h.pin_memory()
-    flm_out_pin = torch.empty_like(flm_pin).pin_memory()
-    maps_out_pin = torch.empty_like(maps_pin).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
-    barrier()
+    map_pin = torch.empty((B, nmw), dtype=torch.complex128).pin_memory()
+    out_pin = torch.empty_like(flm_pin).pin_memory()
+    e2e_steps = max(1, min(K, 3))
+    plan.inverse(flm_pin, out=map_pin)
+    plan.forward(map_pin, out=out_pin)
+    rank_barrier()
     t0 = time.perf_counter()
     e2e_each = []
     for _ in range(e2e_steps):
         ts = time.perf_counter()
-        plan.forward_inverse(maps_pin, flm_pin, flm_out_pin, maps_out_pin)
+        plan.inverse(flm_pin, out=map_pin)
+        plan.forward(map_pin, out=out_pin)
         e2e_each.append(1e3 * (time.perf_counter() - ts))
     torch.cuda.synchronize(dev)
-    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    t_e2e = rank_max(time.perf_counter() - t0, dev)
     e2e_value = whole_job_value(world, B, e2e_steps, t_e2e)
     bytes_flm = B * L * L * 16
     bytes_map = B * nmw * 16
 
-    # rooflines: every stage against its own bound; the dominant one is "roofline"
+    # rooflines per round trip: every stage against its own bound
     pk = peaks()
-    steps = args.steps
     fb = fft_stage_bytes(L, B, args.precision)
+    t = {k: v / 1e3 for k, v in stages.items()}  # seconds per round trip
     stage_roof = {}
-    t = {k: v[0] / 1e3 for k, v in stages.items()}  # seconds over the timed steps
+    sweeps = 2  # one recursion per direction
     if t["delta"] > 0:
-        fl = steps * risbo_units(L) * 7  # one sweep per fused step
+        fl = sweeps * risbo_units(L) * 7
         a = fl / t["delta"] / 1e12
+        a_s = sweeps * 7.0 * L ** 3 / t["delta"] / 1e12
         stage_roof["delta"] = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                                "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep",
-                               "peak_src": "measured (own FP64 DFMA microbenchmark)"}
+                               "peak_src": "measured (own FP64 DFMA microbenchmark)",
+                               "work": "7 flops per octant element of each half-step plane",
+                               "frac_quarter_plane_units": a_s / pk["fp64_tflops"]}
+    tc_flops = 2 * contraction_units(L, spins) * 4
     if t["contract"] > 0:
-        fl = 2 * steps * contraction_units(L, spins) * 4
-        a = fl / t["contract"] / 1e12
+        a = tc_flops / t["contract"] / 1e12
         if args.precision == "mixed":
             stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                                       "frac": a / pk["bf16_tflops"], "kernel": "k_tc_forward/k_tc_inverse",
@@ -283,32 +290,48 @@ def run_ours(args, rank, world, local_rank):
                                                   "same FP64 pipe as DFMA on this part)"}
     for k in ("theta", "phi"):
         if t[k] > 0:
-            a = steps * fb[k] / t[k] / 1e9
+            a = fb[k] / t[k] / 1e9
             stage_roof[k] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
                              "frac": a / pk["hbm_gbs"], "peak_src": pk["src"]}
-    dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k][0])
+    # the Delta stage (recursion + contractions) against max(recursion / FP64,
+    # split tensor products / BF16, plane staging / HBM)
+    staging = sweeps * 4.0 * sum((l + 1) ** 2 for l in range(L)) * (1 + len({s for s in spins}))
+    tc_split = tc_flops * (6 if args.precision == "mixed" else 1)
+    tc_peak = pk["bf16_tflops"] if args.precision == "mixed" else 1.045
+    t_d = t["delta"] + t["contract"]
+    bounds_oct = (sweeps * risbo_units(L) * 7 / (pk["fp64_tflops"] * 1e12), tc_split / (tc_peak * 1e12),
+                  staging / (pk["hbm_gbs"] * 1e9))
+    bounds_q = (sweeps * 7.0 * L ** 3 / (pk["fp64_tflops"] * 1e12),) + bounds_oct[1:]
+    delta_stage = {"ms": 1e3 * t_d, "roofline_ms": 1e3 * max(bounds_oct), "frac": max(bounds_oct) / t_d,
+                   "roofline_ms_quarter_plane_units": 1e3 * max(bounds_q), "frac_quarter_plane_units": max(bounds_q) / t_d,
+                   "bounds_ms": {"recursion_fp64": 1e3 * bounds_oct[0], "contraction_tensor": 1e3 * bounds_oct[1],
+                                 "staging_hbm": 1e3 * bounds_oct[2]}}
+    dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k])
     roof = dict(stage_roof[dom])
     roof["stage"] = dom
     roof["traffic"] = None  # DRAM bytes of the current kernel build are in profiles/ when captured
     result = {
-        "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "ms_per_step_median": statistics.median(each),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32+bf16",
         "data": "synthetic (seeded complex Gaussian f_lm, C_l=1/(l+1)^2)",
-        "config": {"workload": f"MW forward of B={B} maps + inverse of B={B} independent f_lm per step, L={L} "
-                               f"(8 maps s=0, 8 maps s=2), one shared Delta recursion", "L": L, "batch": B,
-                   "spins": spins, "precision": args.precision, "l2_flush": "inputs larger than L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"MW round trip (inverse then forward) L={L}, B={B} (8 maps s=0, 8 maps s=2)",
+                   "L": L, "batch": B, "spins": spins, "precision": args.precision,
+                   "l2_flush": "inputs larger than L2", "graph": True, "parallelism": f"replicas x{world}"},
         "roundtrip_rel_err": err,
-        "roundtrip": {"value": whole_job_value(world, B, args.steps, rt_ms / 1e3), "unit": "transforms/s",
-                      "ms_per_step": rt_ms / args.steps, "rel_err": rt_err,
-                      "what": "inverse then forward of its output (two recursions per step)"},
+        "forward_rate": whole_job_value(world, B, K, fwd_ms / 1e3) / 2,
+        "inverse_rate": whole_job_value(world, B, K, inv_ms / 1e3) / 2,
+        "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
+                  "ms_per_step": fu_ms / K, "rel_err": fu_err,
+                  "what": "mw_forward_inverse: forward of B maps and inverse of B independent f_lm, one shared recursion"},
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
                 "d2h_bytes_per_step": bytes_map + bytes_flm, "ms_each_step": e2e_each},
-        "gpu_launches": launches_per_step * args.steps,
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "gpu_launches": launches_per_step * K,
+        "stage_ms_per_step": stages,
         "roofline": roof,
         "stage_roofline": stage_roof,
+        "delta_stage": delta_stage,
         "clocks": ck,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -356,7 +379,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
