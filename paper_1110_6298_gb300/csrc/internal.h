@@ -69,6 +69,7 @@ struct mw_plan {
   int* d_err = nullptr;            // device error word (bit 0: tensor-core wait, bit 1: grid barrier)
   int* d_prog = nullptr;           // per-tile progress counters of the persistent Risbo kernel
   int risbo_grid = 0;              // co-resident blocks of the persistent Risbo kernel
+  int* d_perm = nullptr;           // placement-aware rank of each Risbo block
   double* d_H = nullptr;           // [LD][LD] half-integer plane
   int LD = 0;                      // plane row stride (L+1)
   double2* d_map_stage = nullptr;  // host-pointer staging
@@ -128,6 +129,7 @@ cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cud
 // owner o) and the contractions of the consumer plans cs[0..nc).
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
 int risbo_blocks_per_sm();
+cudaError_t make_risbo_perm(mw_plan* p);
 
 // One consumer of a Risbo sweep: plan q's forward contraction (mode 0, G+ in
 // q's workspace -> flm_out) or inverse contraction (mode 1, flm_in -> F+ in q's

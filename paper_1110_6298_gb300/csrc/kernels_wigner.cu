@@ -23,8 +23,11 @@
 // they run over m' >= 0 only, and read Delta_{m'm} from row |m| of the quarter
 // plane through the transpose symmetry, so every access is a contiguous row
 // segment.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -87,6 +90,8 @@ struct RisboArgs {
   const double* rscale;  // 1 / (sqrt2 two_jp)
   int* prog;          // per-tile progress: last plane l published
   int* err;
+  const int* perm;    // rank of each block in the tile assignment (null: blockIdx.x)
+  int* smid_out;      // when set: record each block's SM id (placement probe)
 };
 
 // Value of the integer plane Delta^{l-1} (j = l-1, quarter storage, lower
@@ -151,6 +156,15 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
   const int LD = A.LD;
   const size_t plane = (size_t)LD * LD;
   const int G = gridDim.x;
+  if (A.smid_out && tid == 0) {
+    unsigned sid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sid));
+    A.smid_out[blockIdx.x] = (int)sid;
+  }
+  // Block ranks 0..#SM-1 are blocks on distinct SMs (see make_risbo_perm), so the
+  // few tiles of the early planes spread over all SMs instead of sharing the
+  // FP64 pipes of the SMs the first block indices land on.
+  const int vrank = A.perm ? A.perm[blockIdx.x] : (int)blockIdx.x;
   for (int l = l_begin; l < l_end; ++l) {
     const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
     const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
     const int T = (nnew + kRT - 1) / kRT;       // tile rows of plane l
     const int Tp = (l + kRT - 1) / kRT;         // tile rows of plane l-1 (size l)
     const int ntiles = T * (T + 1) / 2;
-    for (int tb = blockIdx.x; tb < ntiles; tb += kPair * G) {
+    for (int tb = vrank; tb < ntiles; tb += kPair * G) {
       int tt[kPair], II[kPair], JJ[kPair];
       int np = 0;
 #pragma unroll
@@ -405,6 +419,7 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
   RisboArgs a;
   a.S = S; a.nslot = nslot; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
   a.sq = p->d_sqrt; a.rsq = p->d_rsqrt; a.rscale = p->d_rscale; a.prog = p->d_prog; a.err = p->d_err;
+  a.perm = p->d_perm; a.smid_out = nullptr;
   void* args[] = {&a, &lb, &le};
   e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args,
                                   (size_t)kRisboSmem, st);
@@ -483,6 +498,44 @@ int risbo_blocks_per_sm() {
     if (v >= 1 && v <= 32) cap = v;
   }
   return n < 1 ? 1 : (n > cap ? cap : n);
+}
+
+// Placement-aware block ranks for the sweep of plan p: one empty launch of the
+// sweep kernel records the SM of every block; ranks are then dealt round-robin
+// over the SMs (rank r < #SM on distinct SMs, and so on).  Correctness does not
+// depend on the placement, only the spread of the early, small planes does.
+cudaError_t make_risbo_perm(mw_plan* p) {
+  const int G = p->risbo_grid;
+  int* d_smid = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_smid, sizeof(int) * (size_t)G);
+  if (e != cudaSuccess) return e;
+  RisboArgs a{};
+  a.LD = p->LD;
+  a.smid_out = d_smid;
+  int lb = 1, le = 1;  // no planes: the launch only records the placement
+  void* args[] = {&a, &lb, &le};
+  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(G), dim3(kRThreads), args, (size_t)kRisboSmem, 0);
+  std::vector<int> smid(G, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(smid.data(), d_smid, sizeof(int) * (size_t)G, cudaMemcpyDeviceToHost);
+  cudaFree(d_smid);
+  if (e != cudaSuccess) return e;
+  // blocks grouped by SM (in order of SM id), dealt one per SM per round
+  std::vector<std::pair<int, int>> bys(G);
+  for (int b = 0; b < G; ++b) bys[b] = {smid[b], b};
+  std::sort(bys.begin(), bys.end());
+  std::vector<std::vector<int>> per_sm;
+  for (int i = 0; i < G; ++i) {
+    if (i == 0 || bys[i].first != bys[i - 1].first) per_sm.emplace_back();
+    per_sm.back().push_back(bys[i].second);
+  }
+  std::vector<int> perm(G, -1);
+  int r = 0;
+  for (size_t round = 0; r < G; ++round)
+    for (auto& v : per_sm)
+      if (round < v.size()) perm[v[round]] = r++;
+  e = cudaMalloc((void**)&p->d_perm, sizeof(int) * (size_t)G);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_perm, perm.data(), sizeof(int) * (size_t)G, cudaMemcpyHostToDevice);
+  return e;
 }
 
 cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {

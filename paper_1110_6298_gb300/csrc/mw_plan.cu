@@ -67,11 +67,13 @@ void free_plan(mw_plan* p) {
   if (!p) return;
   for (mw_plan* c : p->subs) free_plan(c);
   for (mw_plan* c : p->twins) free_plan(c);
-  if (p->shared_sweep) { p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; }
+  if (p->shared_sweep) {
+    p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; p->d_perm = nullptr;
+  }
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_rsqrt, p->d_upole,
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
-                  p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff};
+                  p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -256,6 +258,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     p->d_S32 = owner->d_S32;
     p->d_err = owner->d_err;
     p->d_prog = owner->d_prog;
+    p->d_perm = owner->d_perm;
     p->risbo_grid = owner->risbo_grid;
   } else {
     const size_t plane = (size_t)p->LD * p->LD;
@@ -271,6 +274,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
       int nsm = 0;
       chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
       p->risbo_grid = nsm * risbo_blocks_per_sm();
+      if (e == cudaSuccess) chk(make_risbo_perm(p));
     }
   }
   if (e != cudaSuccess) {
