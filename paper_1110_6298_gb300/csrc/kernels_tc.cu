@@ -41,11 +41,11 @@ constexpr int kSmemUsed = 3 * kATile + 3 * kBTile + 64;
 // Requested dynamic shared memory: at least 80 KB so that no more than two
 // blocks share an SM, which keeps 2 x kTmemCols <= 512 TMEM columns.
 constexpr int kSmem = kSmemUsed > 80 * 1024 ? kSmemUsed : 80 * 1024;
-constexpr int kSlots = 6;               // TMEM accumulator slots of kN columns
-constexpr uint32_t kTmemCols = 256;     // >= kSlots * kN, power of two
+constexpr int kSlots = 4;               // TMEM accumulator slots of kN columns
+constexpr uint32_t kTmemCols = 128;     // >= kSlots * kN, power of two
 constexpr uint32_t kMaxPolls = 1u << 26;
 // split pairs (A part, B part) of the six products, largest first, and the
-// TMEM slot each goes to (slot ks for hi.hi of K step ks, 4 and 5 for the
+// TMEM slot each goes to (slot ks/2 for hi.hi of K steps ks, 2 and 3 for the
 // two correction classes)
 __device__ __forceinline__ int split_a(int p) { return (0x210100 >> (4 * p)) & 0xF; }  // 0,0,1,0,1,2
 __device__ __forceinline__ int split_b(int p) { return (0x012010 >> (4 * p)) & 0xF; }  // 0,1,0,2,1,0
@@ -69,8 +69,16 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
   l = t - (h - s);
 }
 
-// Issue the 4 K steps x 6 split products of one 64-wide K tile into the six
-// accumulator slots (every slot starts fresh in each tile).
+// Slot and accumulate flag of split product p in K step ks of a 64-wide K tile:
+// the hi.hi products of K steps 2q and 2q+1 go to slot q (fresh at 2q), the
+// correction products (2^-8 and 2^-16 smaller) accumulate in slots 2 and 3;
+// every slot starts fresh in each tile.
+__device__ __forceinline__ int slot_of(int p, int ks) { return (p == 0) ? (ks >> 1) : (p < 3 ? 2 : 3); }
+__device__ __forceinline__ int acc_of(int p, int ks) {
+  return (p == 0) ? (ks & 1) : ((ks == 0 && (p == 1 || p == 3)) ? 0 : 1);
+}
+
+// Issue the 4 K steps x 6 split products of one 64-wide K tile (K-major A).
 __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t sb, uint32_t idesc) {
 #pragma unroll
   for (int ks = 0; ks < kKTile / 16; ++ks) {
@@ -78,35 +86,29 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sa, uint32_t 
     for (int p = 0; p < 6; ++p) {
       const uint64_t ad = umma::smem_desc(sa + split_a(p) * kATile + ks * 256, 128, (kKTile / 8) * 128);
       const uint64_t bd = umma::smem_desc(sb + split_b(p) * kBTile + ks * 256, 128, (kKTile / 8) * 128);
-      const int slot = (p == 0) ? ks : (p < 3 ? 4 : 5);
-      const int acc = (p == 0) ? 0 : ((ks == 0 && (p == 1 || p == 3)) ? 0 : 1);
-      umma::mma_bf16(tmem + (uint32_t)(slot * kN), ad, bd, idesc, acc);
+      umma::mma_bf16(tmem + (uint32_t)(slot_of(p, ks) * kN), ad, bd, idesc, acc_of(p, ks));
     }
   }
 }
 
-// Add the six slots into float-float accumulators: warp quadrant q owns TMEM
+// Add the four slots into float-float accumulators: warp quadrant q owns TMEM
 // lanes (tile rows) 32q..32q+31, half h owns columns 16h..16h+15 of each slot.
-// The four hi.hi slots go through TwoSum; the two correction slots (at most
+// The two hi.hi slots go through TwoSum; the two correction slots (at most
 // 2^-8 of the sum) are added to the low word directly, where their own
 // rounding is below 2^-32 of the result.  Loads are issued in pairs.
 __device__ __forceinline__ void drain_half(uint32_t tmem, int quad, int half, float* hi, float* lo) {
   const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(16 * half);
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    uint32_t a[16], b[16];
-    umma::ld_32x32b_x16_async(base + (uint32_t)(2 * sp * kN), a);
-    umma::ld_32x32b_x16_async(base + (uint32_t)((2 * sp + 1) * kN), b);
-    umma::wait_ld();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      two_sum_acc(hi[j], lo[j], __uint_as_float(a[j]));
-      two_sum_acc(hi[j], lo[j], __uint_as_float(b[j]));
-    }
-  }
   uint32_t a[16], b[16];
-  umma::ld_32x32b_x16_async(base + (uint32_t)(4 * kN), a);
-  umma::ld_32x32b_x16_async(base + (uint32_t)(5 * kN), b);
+  umma::ld_32x32b_x16_async(base, a);
+  umma::ld_32x32b_x16_async(base + (uint32_t)kN, b);
+  umma::wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    two_sum_acc(hi[j], lo[j], __uint_as_float(a[j]));
+    two_sum_acc(hi[j], lo[j], __uint_as_float(b[j]));
+  }
+  umma::ld_32x32b_x16_async(base + (uint32_t)(2 * kN), a);
+  umma::ld_32x32b_x16_async(base + (uint32_t)(3 * kN), b);
   umma::wait_ld();
 #pragma unroll
   for (int j = 0; j < 16; ++j) lo[j] += __uint_as_float(a[j]) + __uint_as_float(b[j]);
@@ -130,17 +132,23 @@ __device__ __forceinline__ bool wait_all(uint64_t* mbar, uint32_t phase) {
 
 constexpr int kThreads = 256;  // 8 warps: warp w drains TMEM lanes 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15
 
-// 8 FP32 values -> three 16-byte rows of bf16 (hi, mid, lo) at byte offset off of each split tile
+// 8 FP32 values -> three 16-byte rows of bf16 (hi, mid, lo) at byte offset off
+// of each split tile; pairs are converted with one packed round-to-nearest
+// conversion each (x ~= hi + mid + lo as in umma::split3, element 2i in the
+// low half of word i)
 __device__ __forceinline__ void store_split8(unsigned char* base, int tile_bytes, int off, const float* x) {
   uint32_t h[4], m[4], l[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-    umma::split3(x[2 * i], h0, m0, l0);
-    umma::split3(x[2 * i + 1], h1, m1, l1);
-    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    m[i] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
-    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    const __nv_bfloat162 hp = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(hp);
+    const float r0 = x[2 * i] - hf.x, r1 = x[2 * i + 1] - hf.y;
+    const __nv_bfloat162 mp = __floats2bfloat162_rn(r0, r1);
+    const float2 mf = __bfloat1622float2(mp);
+    const __nv_bfloat162 lp = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+    h[i] = *reinterpret_cast<const uint32_t*>(&hp);
+    m[i] = *reinterpret_cast<const uint32_t*>(&mp);
+    l[i] = *reinterpret_cast<const uint32_t*>(&lp);
   }
   *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(base + tile_bytes + off) = make_uint4(m[0], m[1], m[2], m[3]);
@@ -399,9 +407,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restr
               umma::smem_desc(umma::smem_u32(sA) + split_a(p) * kATile + ks * 2 * kMnLbo, kMnLbo, kMnSbo);
           const uint64_t bd =
               umma::smem_desc(umma::smem_u32(sB) + split_b(p) * kBTile + ks * 256, 128, (kKTile / 8) * 128);
-          const int slt = (p == 0) ? ks : (p < 3 ? 4 : 5);
-          const int acc = (p == 0) ? 0 : ((ks == 0 && (p == 1 || p == 3)) ? 0 : 1);
-          umma::mma_bf16(tmem + (uint32_t)(slt * kN), ad, bd, idesc, acc);
+          umma::mma_bf16(tmem + (uint32_t)(slot_of(p, ks) * kN), ad, bd, idesc, acc_of(p, ks));
         }
       }
       umma::commit(mbar);
