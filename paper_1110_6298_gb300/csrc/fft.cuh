@@ -11,7 +11,8 @@
 // overwrite the inputs, so one shared buffer of n elements suffices.  Other odd
 // primes (the 2L-1 lengths contain factors such as 13, 31, 73 or 127) use a
 // dot-product stage in which each output is an R-term sum; no Bluestein step is
-// needed.  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
+// needed.  The out-of-place (ping-pong) variant also has register butterflies
+// for 11 and 13 (4095 = 3^2 5 7 13 at L = 2048).  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
 #pragma once
 #include <cuda_runtime.h>
 #include "internal.h"
@@ -53,6 +54,26 @@ __device__ __forceinline__ double cs7(int k) {
 __device__ __forceinline__ double sn7(int k) {
   return k == 1 ? 0.78183148246802980871 : (k == 2 ? 0.97492791218182360702 : 0.43388373911755812048);
 }
+__device__ __forceinline__ double cs11(int k) {
+  constexpr double c[5] = {0.841253532831181168862, 0.415415013001886425529, -0.142314838273285140444,
+                           -0.654860733945285064057, -0.95949297361449738989};
+  return c[k - 1];
+}
+__device__ __forceinline__ double sn11(int k) {
+  constexpr double c[5] = {0.540640817455597582108, 0.909631995354518371412, 0.989821441880932732376,
+                           0.755749574354258283774, 0.281732556841429697711};
+  return c[k - 1];
+}
+__device__ __forceinline__ double cs13(int k) {
+  constexpr double c[6] = {0.8854560256532098959, 0.568064746731155802512, 0.120536680255323053349,
+                           -0.35460488704253562597, -0.748510748171101098635, -0.970941817426052027157};
+  return c[k - 1];
+}
+__device__ __forceinline__ double sn13(int k) {
+  constexpr double c[6] = {0.464723172043768545656, 0.82298386589365639458, 0.992708874098053992801,
+                           0.93501624268541482344, 0.663122658240795202377, 0.239315664287557767149};
+  return c[k - 1];
+}
 
 // Odd R-point DFT by the symmetric pairing y_k = a_k +- i b_k with
 // a_k = v_0 + sum_r (v_r + v_{R-r}) cos(2 pi r k/R), b_k = sum_r (v_r - v_{R-r}) sin(2 pi r k/R).
@@ -75,8 +96,8 @@ __device__ __forceinline__ void dft_odd(C<T>* v, bool inv) {
       const int rk = (r * k) % R;
       const int q = rk <= H ? rk : R - rk;         // cos(2pi rk/R) = cos(2pi q/R)
       const T sg = rk <= H ? (T)1 : (T)-1;          // sin flips for rk > R/2
-      const T c = (T)(R == 3 ? cs3(q) : (R == 5 ? cs5(q) : cs7(q)));
-      const T sn = sg * (T)(R == 3 ? sn3(q) : (R == 5 ? sn5(q) : sn7(q)));
+      const T c = (T)(R == 3 ? cs3(q) : (R == 5 ? cs5(q) : (R == 7 ? cs7(q) : (R == 11 ? cs11(q) : cs13(q)))));
+      const T sn = sg * (T)(R == 3 ? sn3(q) : (R == 5 ? sn5(q) : (R == 7 ? sn7(q) : (R == 11 ? sn11(q) : sn13(q)))));
       a.x += s[r - 1].x * c; a.y += s[r - 1].y * c;
       b.x += d[r - 1].x * sn; b.y += d[r - 1].y * sn;
     }
@@ -278,6 +299,8 @@ __device__ typename cplx<T>::t* fft_pp(typename cplx<T>::t* x, typename cplx<T>:
       case 5: fftk::stage_pp<T, 5>(x, y, d.n, Ns, tw, inv); break;
       case 7: fftk::stage_pp<T, 7>(x, y, d.n, Ns, tw, inv); break;
       case 8: fftk::stage_pp<T, 8>(x, y, d.n, Ns, tw, inv); break;
+      case 11: fftk::stage_pp<T, 11>(x, y, d.n, Ns, tw, inv); break;
+      case 13: fftk::stage_pp<T, 13>(x, y, d.n, Ns, tw, inv); break;
       default: fftk::stage_dot_pp<T>(x, y, d.n, Ns, R, tw, inv); break;
     }
     typename cplx<T>::t* t = x;
