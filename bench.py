@@ -36,6 +36,16 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# stage kernels at L = 2048, B = 16, mixed, from one 1-pass ncu capture of
+# this bench (the kernels unchanged since): the sweep's four 512-plane chunks
+# and the contraction's four chunks per direction; None where not captured.
+TRAFFIC_L2048_B16 = {
+    "delta": [0.0, 0.127e9, 1.221e9, 3.451e9],
+    "contract": [0.746e9, 4.946e9, 12.671e9, 23.986e9, 0.454e9, 3.526e9, 9.264e9, 17.619e9],
+}
+
+
 def peaks():
     pk = {"hbm_gbs": 6794.8, "bf16_tflops": 1899.0, "bf16_tflops_sustained": 1700.8, "src": "fallback"}
     try:
@@ -307,9 +317,14 @@ def run_ours(args, rank, world, local_rank):
                    "bounds_ms": {"recursion_fp64": 1e3 * bounds_oct[0], "contraction_tensor": 1e3 * bounds_oct[1],
                                  "staging_hbm": 1e3 * bounds_oct[2]}}
     dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k])
+    if L == 2048 and B == 16 and args.precision == "mixed":
+        for k, v in TRAFFIC_L2048_B16.items():
+            if k in stage_roof:
+                stage_roof[k]["traffic"] = sum(v) / len(v)  # bytes per launch, averaged over the launches
+                stage_roof[k]["traffic_per_step"] = sum(v) * (2 if k == "delta" else 1)
     roof = dict(stage_roof[dom])
     roof["stage"] = dom
-    roof["traffic"] = None  # DRAM bytes of the current kernel build are in profiles/ when captured
+    roof.setdefault("traffic", None)
     result = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "ms_per_step_median": statistics.median(each),
