@@ -64,12 +64,16 @@ typedef enum {
 
 /* Precision of a plan (flags & 0xff).
  * MW_PREC_FP64 : every stage in IEEE double.
- * MW_PREC_MIXED: the Wigner-Delta recursion (Risbo, Sec. V-B) in double; the
- *                Delta contraction on the tensor cores (tcgen05) as split-BF16
- *                products with FP32 accumulation and a double sum across
- *                m'-chunks; the FFT stages in single precision.  Designed for a
- *                relative error below 1e-6 against the FP64 path. */
-enum { MW_PREC_FP64 = 0, MW_PREC_MIXED = 1 };
+ * MW_PREC_MIXED (= MW_PREC_MIXED_BF16X3): the Wigner-Delta recursion (Risbo,
+ *                Sec. V-B) in double; the Delta contraction on the tensor cores
+ *                (tcgen05) with FP32 operands split into three BF16 parts (six
+ *                products), FP32 accumulation and a float-float sum across
+ *                K tiles and chunks; the FFT stages in single precision.
+ * MW_PREC_MIXED_TF32X3: as MW_PREC_MIXED with the operands split into two TF32
+ *                parts (three products: hi.hi, hi.lo, lo.hi).
+ * Both mixed precisions are designed for a relative error below 1e-6 against
+ * the FP64 path. */
+enum { MW_PREC_FP64 = 0, MW_PREC_MIXED = 1, MW_PREC_MIXED_BF16X3 = 1, MW_PREC_MIXED_TF32X3 = 2 };
 
 /* MW_FLAG_GRAPH (or-ed into flags): the first call with a given (direction,
  * input, output) captures the whole call into a CUDA graph, later calls with

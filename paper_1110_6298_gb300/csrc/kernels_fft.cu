@@ -590,6 +590,6 @@ cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st) {
 }
 cudaError_t launch_pole_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st) {
   k_pole_forward_adjoint<<<p->B, 256, 0, st>>>(dims_of(p), p->d_Gp, p->d_upole, map, p->d_moff, p->d_spins,
-                                                p->prec == MW_PREC_MIXED ? 1 : 0);
+                                                p->prec != MW_PREC_FP64 ? 1 : 0);
   return cudaGetLastError();
 }

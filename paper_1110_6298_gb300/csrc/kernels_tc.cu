@@ -155,6 +155,72 @@ __device__ __forceinline__ void store_split8(unsigned char* base, int tile_bytes
   *reinterpret_cast<uint4*>(base + 2 * tile_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// ---- TF32 x3 variant: x = hi + lo, each a TF32 value (11 significant bits);
+// products hi.hi, hi.lo, lo.hi (K = 8 per MMA).  Tiles are K-major with 4
+// values per 16-byte core-matrix row.
+constexpr int kATile32 = 128 * kKTile * 4;  // bytes of one TF32 A split (32 KB)
+constexpr int kBTile32 = kN * kKTile * 4;   // bytes of one TF32 B split (8 KB)
+constexpr int kSmem32 = 2 * kATile32 + 2 * kBTile32 + 64;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// byte offset of element (r, k) of a K-major TF32 tile of kKTile columns
+__device__ __forceinline__ int tile_off32(int r, int k) {
+  return (r >> 3) * ((kKTile / 4) * 128) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+// 4 FP32 values (consecutive K of one row) -> the 16-byte rows of the hi and
+// lo tiles at byte offset off
+__device__ __forceinline__ void store_split4_tf32(unsigned char* base, int tile_bytes, int off, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = to_tf32(x[i]);
+    l[i] = to_tf32(x[i] - __uint_as_float(h[i]));
+  }
+  *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(base + tile_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// 8 consecutive K values of row r starting at k0 (a multiple of 8)
+__device__ __forceinline__ void store_split8_tf32(unsigned char* base, int tile_bytes, int r, int k0, const float* x) {
+  store_split4_tf32(base, tile_bytes, tile_off32(r, k0), x);
+  store_split4_tf32(base, tile_bytes, tile_off32(r, k0 + 4), x + 4);
+}
+// The 8 K steps x 3 products of one 64-wide K tile: hi.hi of steps 4q..4q+3
+// into slot q (fresh at 4q), hi.lo and lo.hi (2^-11 smaller) into slot 2.
+__device__ __forceinline__ void issue_tile_tf32(uint32_t tmem, uint32_t sa, uint32_t sb, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < kKTile / 8; ++ks) {
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int pa = (p == 2) ? 1 : 0, pb = (p == 1) ? 1 : 0;
+      const uint64_t ad = umma::smem_desc(sa + pa * kATile32 + ks * 256, 128, (kKTile / 4) * 128);
+      const uint64_t bd = umma::smem_desc(sb + pb * kBTile32 + ks * 256, 128, (kKTile / 4) * 128);
+      const int slot = (p == 0) ? (ks >> 2) : 2;
+      const int acc = (p == 0) ? ((ks & 3) != 0) : ((ks == 0 && p == 1) ? 0 : 1);
+      umma::mma_tf32(tmem + (uint32_t)(slot * kN), ad, bd, idesc, acc);
+    }
+  }
+}
+// Drain of the three TF32 slots: two hi.hi slots through TwoSum, the
+// correction slot added to the low word.
+__device__ __forceinline__ void drain_tf32(uint32_t tmem, int quad, int half, float* hi, float* lo) {
+  const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(16 * half);
+  uint32_t a[16], b[16], c[16];
+  umma::ld_32x32b_x16_async(base, a);
+  umma::ld_32x32b_x16_async(base + (uint32_t)kN, b);
+  umma::ld_32x32b_x16_async(base + (uint32_t)(2 * kN), c);
+  umma::wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    two_sum_acc(hi[j], lo[j], __uint_as_float(a[j]));
+    two_sum_acc(hi[j], lo[j], __uint_as_float(b[j]));
+    lo[j] += __uint_as_float(c[j]);
+  }
+}
+
 // 8 consecutive floats from a 32-byte aligned address
 __device__ __forceinline__ void load8(const float* __restrict__ p, float* v) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
@@ -182,6 +248,7 @@ __device__ __forceinline__ void kernel8(const float* __restrict__ P, int LD, int
 // ---------------------------------------------------------------------------
 // forward: f_lm for l in [l0, l1), both signs of m = +-am, every spin group
 // ---------------------------------------------------------------------------
+template <bool TF>
 __global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restrict__ S, int LD, int L, int M, int l0,
                                                          int l1, const SpinGroup* __restrict__ groups, int ng,
                                                          const float2* __restrict__ Gp,
@@ -189,9 +256,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restr
                                                          double2* __restrict__ flm, const long long* __restrict__ foff,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int aT = TF ? kATile32 : kATile, bT = TF ? kBTile32 : kBTile, np = TF ? 2 : 3;
   unsigned char* sA = smem;
-  unsigned char* sB = smem + 3 * kATile;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 3 * kATile + 3 * kBTile);
+  unsigned char* sB = smem + np * aT;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + np * aT + np * bT);
   uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int am = blockIdx.x;
   const int lt0 = l0 + 128 * blockIdx.y;           // rows l of this block: [lt0, lt1)
@@ -203,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restr
   if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
   sync_all();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = umma::idesc_bf16_f32(128, kN);
+  const uint32_t idesc = TF ? umma::idesc_tf32_f32(128, kN) : umma::idesc_bf16_f32(128, kN);
   const size_t plane = (size_t)LD * LD;
   uint32_t phase = 0;
   bool ok = true;
@@ -258,20 +326,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restr
       };
       gather(0);
       for (int mp0 = 0; mp0 < lt1; mp0 += kKTile) {
+        if constexpr (TF) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) store_split8(sA, kATile, umma::tile_off(r0 + 32 * k, 8 * cq, kKTile / 8), xa[k]);
-        store_split8(sB, kBTile, umma::tile_off(r0, 8 * cq, kKTile / 8), xb);
+          for (int k = 0; k < 4; ++k) store_split8_tf32(sA, kATile32, r0 + 32 * k, 8 * cq, xa[k]);
+          store_split8_tf32(sB, kBTile32, r0, 8 * cq, xb);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) store_split8(sA, kATile, umma::tile_off(r0 + 32 * k, 8 * cq, kKTile / 8), xa[k]);
+          store_split8(sB, kBTile, umma::tile_off(r0, 8 * cq, kKTile / 8), xb);
+        }
         umma::fence_proxy_async();
         sync_all();
         if (tid == 0) {
-          issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+          if constexpr (TF) issue_tile_tf32(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+          else issue_tile(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
           umma::commit(mbar);
         }
         if (mp0 + kKTile < lt1) gather(mp0 + kKTile);
         const bool w = wait_all(mbar, phase);
         phase ^= 1u;
         ok = ok && w;
-        if (w) drain_half(tmem, quad, half, ahi, alo);
+        if (w) {
+          if constexpr (TF) drain_tf32(tmem, quad, half, ahi, alo);
+          else drain_half(tmem, quad, half, ahi, alo);
+        }
         sync_all();
       }
     }
@@ -320,14 +398,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_forward(const float* __restr
 constexpr int kMnSbo = 128;                  // stride between 8-m' groups
 constexpr int kMnLbo = (128 / 8) * 128;      // stride between 8-l groups (2048)
 
+template <bool TF>
 __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restrict__ S, int LD, int L, int M, int l0,
                                                          int l1, const SpinGroup* __restrict__ groups,
                                                          const float2* __restrict__ flmf, double2* __restrict__ Fp,
                                                          int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int aT = TF ? kATile32 : kATile, bT = TF ? kBTile32 : kBTile, np = TF ? 2 : 3;
   unsigned char* sA = smem;
-  unsigned char* sB = smem + 3 * kATile;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 3 * kATile + 3 * kBTile);
+  unsigned char* sB = smem + np * aT;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + np * aT + np * bT);
   uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int am = blockIdx.x, mp0 = blockIdx.y * 128;
   const SpinGroup& g = groups[blockIdx.z];
@@ -340,7 +420,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restr
   if (warp == 0) umma::tmem_alloc(slot, kTmemCols);
   sync_all();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = umma::idesc_bf16_f32(128, kN) | (1u << 15);  // A MN-major
+  // BF16: A MN-major (plane rows are contiguous in m'); TF32: A K-major
+  const uint32_t idesc = TF ? umma::idesc_tf32_f32(128, kN) : (umma::idesc_bf16_f32(128, kN) | (1u << 15));
   const size_t plane = (size_t)LD * LD;
   uint32_t phase = 0;
   bool ok = true;
@@ -352,19 +433,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restr
   // consecutive l (one MN-major core matrix: conflict-free 16-byte stores), the
   // lane octets consecutive chunks.  The next tile is gathered into registers
   // while the current tile's MMAs and drain run.
+  // (TF32: thread tid stages row m' = mp0 + (tid & 127) of A for the l groups
+  // 4 ((tid >> 7) + 2q), q < 8 -- 8 lanes = 8 rows of one K-major core matrix.)
   const int k0 = (tid & 7) + 8 * (tid >> 7), cA = (tid >> 3) & 15;
   const int n0 = (tid & 7) + 8 * (tid >> 6), cB = (tid >> 3) & 7;
+  const int mrow = tid & 127, g0 = tid >> 7;
   float xa[4][8], xb[8];
   auto gather = [&](int lb) {
-    const int mp = mp0 + 8 * cA;
+    if constexpr (TF) {
+      const int mp = mp0 + mrow;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int l = lb + k0 + 16 * q;
-      if (l >= lstart && l < l1 && mp <= l && mp < L) {
-        kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, xa[q]);
-      } else {
+      for (int q = 0; q < 8; ++q) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) xa[q][i] = 0.f;
+        for (int i = 0; i < 4; ++i) {
+          const int l = lb + 4 * (g0 + 2 * q) + i;
+          float v = 0.f;
+          if (l >= lstart && l < l1 && mp <= l && mp < L) {
+            const float* P = S + (size_t)(l - l0) * plane;
+            v = __ldg(P + (size_t)am * LD + mp) * __ldg(P + (size_t)as * LD + mp);
+            if ((am + as + (s > 0 ? l + mp : 0)) & 1) v = -v;
+          }
+          xa[q >> 1][4 * (q & 1) + i] = v;
+        }
+      }
+    } else {
+      const int mp = mp0 + 8 * cA;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = lb + k0 + 16 * q;
+        if (l >= lstart && l < l1 && mp <= l && mp < L) {
+          kernel8(S + (size_t)(l - l0) * plane, LD, am, as, s, l, mp, xa[q]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) xa[q][i] = 0.f;
+        }
       }
     }
     const int j = n0 >> 1;
@@ -390,15 +492,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restr
   gather(l0);
   for (int kt = 0; kt * kKTile < l1 - l0; ++kt) {
     const int lb = l0 + kt * kKTile;
+    if constexpr (TF) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = k0 + 16 * q;
-      store_split8(sA, kATile, cA * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, xa[q]);
+      for (int q = 0; q < 8; ++q)
+        store_split4_tf32(sA, kATile32, tile_off32(mrow, 4 * (g0 + 2 * q)), &xa[q >> 1][4 * (q & 1)]);
+      store_split8_tf32(sB, kBTile32, n0, 8 * cB, xb);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + 16 * q;
+        store_split8(sA, kATile, cA * kMnSbo + (k >> 3) * kMnLbo + (k & 7) * 16, xa[q]);
+      }
+      store_split8(sB, kBTile, umma::tile_off(n0, 8 * cB, kKTile / 8), xb);
     }
-    store_split8(sB, kBTile, umma::tile_off(n0, 8 * cB, kKTile / 8), xb);
     umma::fence_proxy_async();
     sync_all();
-    if (tid == 0) {
+    if (tid == 0 && TF) {
+      issue_tile_tf32(tmem, umma::smem_u32(sA), umma::smem_u32(sB), idesc);
+      umma::commit(mbar);
+    } else if (tid == 0) {
 #pragma unroll
       for (int ks = 0; ks < kKTile / 16; ++ks) {
 #pragma unroll
@@ -417,7 +529,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_inverse(const float* __restr
     phase ^= 1u;
     ok = ok && w;
     if (!ok) break;
-    drain_half(tmem, quad, half, ahi, alo);
+    if constexpr (TF) drain_tf32(tmem, quad, half, ahi, alo);
+    else drain_half(tmem, quad, half, ahi, alo);
     sync_all();
   }
   // epilogue: add the chunk's sum into the FP64 accumulator F+
@@ -464,20 +577,35 @@ cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+template <bool TF>
+cudaError_t tc_forward_t(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
+  const int sm = TF ? kSmem32 : kSmem;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_forward<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
   const dim3 grid(l1, (l1 - l0 + 127) / 128);
-  k_tc_forward<<<grid, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, (int)p->groups.size(),
-                                       reinterpret_cast<const float2*>(p->d_Gp), p->d_nl, flm, p->d_foff, p->d_err);
+  k_tc_forward<TF><<<grid, kThreads, sm, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups,
+                                               (int)p->groups.size(), reinterpret_cast<const float2*>(p->d_Gp),
+                                               p->d_nl, flm, p->d_foff, p->d_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const float2* flm, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+template <bool TF>
+cudaError_t tc_inverse_t(const mw_plan* p, int l0, int l1, const float2* flm, cudaStream_t st) {
+  const int sm = TF ? kSmem32 : kSmem;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_inverse<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
   const dim3 grid(l1, (l1 + 127) / 128, (unsigned)p->groups.size());
-  k_tc_inverse<<<grid, kThreads, kSmem, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, flm,
-                                         reinterpret_cast<double2*>(p->d_Gp), p->d_err);
+  k_tc_inverse<TF><<<grid, kThreads, sm, st>>>(p->d_S32, p->LD, p->L, p->M, l0, l1, p->d_groups, flm,
+                                               reinterpret_cast<double2*>(p->d_Gp), p->d_err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tc_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st) {
+  return p->prec == MW_PREC_MIXED_TF32X3 ? tc_forward_t<true>(p, l0, l1, flm, st)
+                                         : tc_forward_t<false>(p, l0, l1, flm, st);
+}
+
+cudaError_t launch_tc_inverse(const mw_plan* p, int l0, int l1, const float2* flm, cudaStream_t st) {
+  return p->prec == MW_PREC_MIXED_TF32X3 ? tc_inverse_t<true>(p, l0, l1, flm, st)
+                                         : tc_inverse_t<false>(p, l0, l1, flm, st);
 }

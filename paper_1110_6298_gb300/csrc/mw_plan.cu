@@ -99,7 +99,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   *out = nullptr;
   if (L < 1 || L > 2048 || B < 1 || !spins) return MW_EINVAL;
   const int prec = (int)(flags & 0xffu);
-  if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED) return MW_EINVAL;
+  if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED && prec != MW_PREC_MIXED_TF32X3) return MW_EINVAL;
   if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH)) return MW_EINVAL;
   for (int b = 0; b < B; ++b)
     if (spins[b] <= -L || spins[b] >= L) return MW_EINVAL;

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmw.so")
 
 MW_OK, MW_EINVAL, MW_ENOMEM, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = range(6)
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_bf16": 1, "mixed_tf32": 2}
 FLAG_GRAPH = 1 << 8
 
 _lib = None

@@ -32,7 +32,7 @@ def inputs(mw, L, spins, seed):
     return torch.from_numpy(maps).cuda(), torch.from_numpy(flm).cuda()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_tf32"])
 @pytest.mark.parametrize("L,spins", [(1, [0]), (7, [0, -2]), (130, [1, 0, 2]), (300, [0] * 9 + [2])])
 def test_fused_equals_separate_calls(mw, precision, L, spins):
     maps, flm = inputs(mw, L, spins, L)

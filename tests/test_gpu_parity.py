@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
 
 Tolerances (relative max error max|x - x_o| / max|x_o|): 1e-12 for the FP64
-path and 1e-6 for the mixed path.  Sizes span several 64-wide tiles / chunks
+path and 1e-6 for both mixed paths (BF16x3 and TF32x3 contractions).  Sizes span several 64-wide tiles / chunks
 with ragged tails (L = 65, 130, 200), the degenerate cases (L = 1, L = 2, |s| =
 L-1), batches of mixed spin, host and device pointers, and the full
 L = 2048 x 16 workload on sampled outputs.
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 from paper_1110_6298_gb300 import workloads as wl  # noqa: E402
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "mixed_tf32": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +60,7 @@ CASES = [(1, [0]), (2, [1, 0, -1]), (3, [0, 2]), (7, [-3]), (32, [0]), (65, [2, 
          (200, [-2, 5])]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tf32"])
 @pytest.mark.parametrize("L,spins", CASES)
 def test_inverse(mw, prec, L, spins):
     flm = rand_flm_batch(L, spins, L)
@@ -70,7 +70,7 @@ def test_inverse(mw, prec, L, spins):
     assert relmax(got, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tf32"])
 @pytest.mark.parametrize("L,spins", CASES)
 def test_forward_non_bandlimited(mw, prec, L, spins):
     x = rand_map_batch(L, len(spins), L)
@@ -83,7 +83,7 @@ def test_forward_non_bandlimited(mw, prec, L, spins):
         assert np.all(got[b][ell < abs(s)] == 0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tf32"])
 @pytest.mark.parametrize("L,spins", [(2, [1]), (9, [0, -2]), (65, [3, 0]), (130, [-1])])
 def test_adjoints(mw, prec, L, spins):
     plan = mw.Plan(L, spins, precision=prec)
@@ -150,7 +150,7 @@ def test_rejects_bad_arguments(mw):
         plan.forward(torch.zeros(5, dtype=torch.complex128, device="cuda"))
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_tf32", "fp64"])
 def test_full_size_l2048_b16_sampled(mw, prec):
     """The benchmarked workload (L = 2048, 16 maps: 8 of spin 0, 8 of spin 2),
     in the benchmark's launch configuration, checked on sampled outputs: the
