@@ -403,6 +403,78 @@ def inverse_adjoint(x, L, s):
 
 
 # --------------------------------------------------------------------------
+# Quadrature (Sec. IV-F, Eq. quadrature)
+# --------------------------------------------------------------------------
+
+def quadrature_sample_count(L):
+    """L(L-1) + 1 samples: L-1 rings of L samples in phi and the pole (Sec. IV-F)."""
+    return L * (L - 1) + 1
+
+
+def quadrature_phi_nodes(L):
+    """phi'_p = 2 pi p / L, p = 0..L-1 (Sec. IV-F)."""
+    return 2 * np.pi * np.arange(L) / L
+
+
+def quadrature_v(L):
+    """v(theta_t) = 1/(2L-1) sum_{|m'| <= L-1} w(-m') e^{i m' theta_t} on the
+    extended nodes t = 0..2L-2 (Sec. IV-F, second display).  Real by the
+    symmetry of w; the real part is returned."""
+    mp = np.arange(-(L - 1), L)
+    th = theta_nodes(L, extended=True)
+    v = (weight(-mp)[None, :] * np.exp(1j * np.outer(th, mp))).sum(axis=1) / (2 * L - 1)
+    return v.real
+
+
+def quadrature_weights(L, s=0):
+    """q(theta_t), t = 0..L-1 (Sec. IV-F, first display):
+    q_t = (2 pi / L) [ v(theta_t) + (1 - delta_{t,L-1}) (-1)^s v(theta_{2L-2-t}) ],
+    reading the garbled Kronecker delta as delta_{t,L-1}."""
+    v = quadrature_v(L)
+    t = np.arange(L)
+    sg = -1.0 if (s % 2) else 1.0
+    fold = np.where(t == L - 1, 0.0, sg * v[2 * L - 2 - t])
+    return 2 * np.pi / L * (v[:L] + fold)
+
+
+def quadrature_integrate(f_q, L, s=0):
+    """I = sum_{t,p} f(theta_t, phi'_p) q(theta_t) (Eq. quadrature) for maps in
+    the quadrature layout: rings t = 0..L-2 of L samples at phi'_p, then one pole
+    sample f(pi, 0); on the pole ring f(pi, phi) = f(pi, 0) e^{i s phi}, so its L
+    samples sum to L f(pi, 0) for s = 0 and to 0 otherwise (|s| < L).
+    f_q: [n] or [B, n] with n = L(L-1)+1.  Returns a complex scalar per map."""
+    f_q = np.asarray(f_q, dtype=np.complex128)
+    single = f_q.ndim == 1
+    fb = f_q[None] if single else f_q
+    q = quadrature_weights(L, s)
+    rings = fb[:, : (L - 1) * L].reshape(fb.shape[0], L - 1, L)
+    out = (rings.sum(axis=2) * q[None, : L - 1]).sum(axis=1)
+    if s == 0:
+        out = out + q[L - 1] * L * fb[:, (L - 1) * L]
+    return out[0] if single else out
+
+
+def quadrature_samples(flm, L, s):
+    """Band-limited f on the quadrature grid: the rings on the MW phi nodes
+    (inverse_rings, Eqs. Fmm, Fmt, f_pfft), their phi coefficients F_m(theta_t)
+    (a length-(2L-1) DFT, exact for |m| <= L-1), then f(theta_t, phi'_p) =
+    sum_m F_m(theta_t) e^{i m phi'_p} summed directly.  Returns the quadrature
+    layout (L-1 rings, then the pole)."""
+    flm = np.asarray(flm, dtype=np.complex128)
+    M = 2 * L - 1
+    rings_mw = inverse_rings(flm, L, s, np.arange(L))    # [L][M]: f(theta_t, phi_p)
+    Fk = sfft.fft(rings_mw, axis=1) / M                 # [L][M]: F_m at index m mod M
+    m = np.arange(-(L - 1), L)
+    Fmt = Fk[:, m % M]
+    ph = quadrature_phi_nodes(L)
+    rings = Fmt @ np.exp(1j * np.outer(m, ph))           # [L][L]
+    out = np.empty(quadrature_sample_count(L), dtype=np.complex128)
+    out[: (L - 1) * L] = rings[: L - 1].ravel()
+    out[(L - 1) * L] = rings[L - 1, 0]
+    return out
+
+
+# --------------------------------------------------------------------------
 # Error measures (relative max and relative RMS, plus the paper's max-abs)
 # --------------------------------------------------------------------------
 
