@@ -249,6 +249,17 @@ def run_ours(args, rank, world, local_rank):
     fu_err = float((fu_flm - flm2).abs().max().item() / flm2.abs().max().item())
     del flm2, maps_in, fu_flm, fu_map
 
+    # quadrature rule (Sec. IV-F): integrals of B maps in the quadrature layout
+    gq = torch.Generator(device=dev)
+    gq.manual_seed(11106298)
+    mq = torch.randn((B, mw.quadrature_size(L)), dtype=torch.complex128, device=dev, generator=gq)
+    qout = torch.empty(B, dtype=torch.complex128, device=dev)
+    plan.quadrature(mq, out=qout)
+    q_ms, _ = timed(lambda: plan.quadrature(mq, out=qout), K)
+    q_bytes = mq.numel() * 16
+    q_gbs = q_bytes * K / (q_ms / 1e3) / 1e9
+    del mq
+
     # end to end: the round trip through the C ABI with pinned host buffers,
     # host<->device copies inside the timed region
     flm_pin = flm_h.pin_memory()
@@ -273,6 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
     # rooflines per round trip: every stage against its own bound
     pk = peaks()
+    pk_hbm = pk["hbm_gbs"]
     fb = fft_stage_bytes(L, B, args.precision)
     t = {k: v / 1e3 for k, v in stages.items()}  # seconds per round trip
     stage_roof = {}
@@ -345,6 +357,10 @@ def run_ours(args, rank, world, local_rank):
         "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
                   "ms_per_step": fu_ms / K, "rel_err": fu_err,
                   "what": "mw_forward_inverse: forward of B maps and inverse of B independent f_lm, one shared recursion"},
+        "quadrature": {"value": world * B * K / (q_ms / 1e3), "unit": "integrals/s", "ms_per_call": q_ms / K,
+                       "what": f"MW quadrature rule, {B} maps of L(L-1)+1 samples per call",
+                       "roofline": {"bound": "hbm", "achieved": q_gbs, "peak": pk_hbm, "unit": "GB/s",
+                                    "frac": q_gbs / pk_hbm, "kernel": "k_quad_partial"}},
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
                 "d2h_bytes_per_step": bytes_map + bytes_flm, "ms_each_step": e2e_each},
         "gpu_launches": launches_per_step * K,

@@ -137,6 +137,25 @@ mw_status mw_forward_inverse(mw_plan *plan, const void *map_in, void *flm_out, c
 mw_status mw_forward_adjoint(mw_plan *plan, const void *flm_in, void *map_out, void *stream);
 mw_status mw_inverse_adjoint(mw_plan *plan, const void *map_in, void *flm_out, void *stream);
 
+/* MW quadrature rule (Sec. IV-F, Eq. quadrature): the integral over the sphere
+ * of a map band-limited at L from L(L-1)+1 samples,
+ *   I = sum_{t<L} sum_{p<L} f(theta_t, 2 pi p / L) q(theta_t),
+ *   q(theta_t) = (2 pi / L) [ v(theta_t) + (1 - delta_{t,L-1}) (-1)^s v(theta_{2L-2-t}) ],
+ *   v(theta_t) = 1/(2L-1) sum_{|m'| <= L-1} w(-m') e^{i m' theta_t}
+ * (the Kronecker delta of the printed formula read as delta_{t,L-1}).
+ * Quadrature layout of a map (complex doubles): rings t = 0..L-2, each with L
+ * samples at phi'_p = 2 pi p / L, then ONE pole sample f(pi, 0) (its ring is
+ * f(pi, 0) e^{i s phi}).
+ * mw_quadrature_weights: q(theta_t), t = 0..L-1, into q_out (L doubles, device
+ *   memory); 1 <= L <= 2048, |s| < L.  Allocates nothing.
+ * mw_quadrature: for a uniform plan (not ragged), the integrals of its batch of
+ *   maps in the quadrature layout, maps_q [batch][L(L-1)+1] -> integrals
+ *   [batch] (complex doubles), both device memory; map b uses spin spins[b].
+ *   The first call allocates the plan's weight table and partial sums.
+ *   Results are bitwise reproducible (fixed-order reductions). */
+mw_status mw_quadrature_weights(int L, int s, double *q_out, void *stream);
+mw_status mw_quadrature(mw_plan *plan, const void *maps_q, void *integrals, void *stream);
+
 /* Wait for the plan's work on `stream` and report device-side errors: returns
  * MW_ETIMEOUT (and clears the flag) if a tensor-core wait inside a kernel gave
  * up since the last check -- the affected outputs are then invalid -- MW_ECUDA

@@ -70,6 +70,8 @@ struct mw_plan {
   int* d_prog = nullptr;           // per-tile progress counters of the persistent Risbo kernel
   int risbo_grid = 0;              // co-resident blocks of the persistent Risbo kernel
   int* d_perm = nullptr;           // placement-aware rank of each Risbo block
+  double* d_qw = nullptr;          // quadrature weights q(theta_t): [even spin][L], [odd spin][L]
+  double2* d_qpart = nullptr;      // quadrature partial sums [B][chunks]
   double* d_H = nullptr;           // [LD][LD] half-integer plane
   int LD = 0;                      // plane row stride (L+1)
   double2* d_map_stage = nullptr;  // host-pointer staging
@@ -129,6 +131,9 @@ cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cud
 // owner o) and the contractions of the consumer plans cs[0..nc).
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
 int risbo_blocks_per_sm();
+int quad_chunks(const mw_plan* p);
+cudaError_t launch_quad_weights(int L, int s, double* q, cudaStream_t st);
+cudaError_t launch_quadrature(const mw_plan* p, const double2* maps, double2* out, cudaStream_t st, int* launches);
 cudaError_t make_risbo_perm(mw_plan* p);
 
 // One consumer of a Risbo sweep: plan q's forward contraction (mode 0, G+ in

@@ -73,7 +73,8 @@ void free_plan(mw_plan* p) {
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_rsqrt, p->d_upole,
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
-                  p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm};
+                  p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
+                  p->d_qw,     p->d_qpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -658,6 +659,36 @@ mw_status mw_forward_inverse(mw_plan* plan, const void* map_in, void* flm_out, c
 }
 mw_status mw_inverse_adjoint(mw_plan* plan, const void* map_in, void* flm_out, void* stream) {
   return run(plan, kInverseAdjoint, map_in, flm_out, stream);
+}
+
+mw_status mw_quadrature_weights(int L, int s, double* q_out, void* stream) {
+  if (L < 1 || L > 2048 || s <= -L || s >= L || !q_out || !is_device_ptr(q_out)) return MW_EINVAL;
+  return from_cuda(launch_quad_weights(L, s, q_out, (cudaStream_t)stream));
+}
+
+mw_status mw_quadrature(mw_plan* plan, const void* maps_q, void* integrals, void* stream) {
+  if (!plan || !maps_q || !integrals) return MW_EINVAL;
+  if (!plan->subs.empty()) return MW_EUNSUPPORTED;
+  if (!is_device_ptr(maps_q) || !is_device_ptr(integrals)) return MW_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!plan->d_qw) {  // weights of even and odd spin, computed once per plan
+    e = cudaMalloc((void**)&plan->d_qw, sizeof(double) * 2 * (size_t)plan->L);
+    if (e == cudaSuccess) e = launch_quad_weights(plan->L, 0, plan->d_qw, st);
+    if (e == cudaSuccess) e = launch_quad_weights(plan->L, 1, plan->d_qw + plan->L, st);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_qpart, sizeof(double2) * (size_t)plan->B * quad_chunks(plan));
+    if (e == cudaSuccess) plan->ws_bytes += sizeof(double) * 2 * plan->L + sizeof(double2) * plan->B * quad_chunks(plan);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(plan->d_qw);
+      plan->d_qw = nullptr;
+      return from_cuda(e);
+    }
+  }
+  int nl = 0;
+  e = launch_quadrature(plan, (const double2*)maps_q, (double2*)integrals, st, &nl);
+  plan->last_launches = nl;
+  return from_cuda(e);
 }
 
 mw_status mw_plan_destroy(mw_plan* plan) {

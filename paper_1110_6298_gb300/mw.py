@@ -68,6 +68,10 @@ def lib():
         L.mw_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           c_int]
         L.mw_plan_stage_times.restype = c_int
+        L.mw_quadrature_weights.argtypes = [c_int, c_int, vp, vp]
+        L.mw_quadrature_weights.restype = c_int
+        L.mw_quadrature.argtypes = [vp, vp, vp, vp]
+        L.mw_quadrature.restype = c_int
         L.mw_forward_inverse.argtypes = [vp, vp, vp, vp, vp, vp]
         L.mw_forward_inverse.restype = c_int
         L.mw_inverse_noalloc.argtypes = [c_int, c_int, vp, vp, vp]
@@ -86,6 +90,20 @@ def map_size(L):
 
 def flm_size(L):
     return int(lib().mw_flm_size(int(L)))
+
+
+def quadrature_size(L):
+    """Samples of a map in the quadrature layout: L(L-1) + 1."""
+    return int(L) * (int(L) - 1) + 1
+
+
+def quadrature_weights(L, s=0, device="cuda"):
+    """q(theta_t), t = 0..L-1, of the MW quadrature rule (Sec. IV-F), computed on the GPU."""
+    q = torch.empty(int(L), dtype=torch.float64, device=device)
+    st = lib().mw_quadrature_weights(int(L), int(s), ctypes.c_void_p(q.data_ptr()), _stream_of(q))
+    if st != MW_OK:
+        raise MWError(st, "mw_quadrature_weights")
+    return q
 
 
 def _stream_of(t):
@@ -215,6 +233,21 @@ class Plan:
         if st != MW_OK:
             raise MWError(st, "mw_forward_inverse")
         return flm_out, map_out
+
+    def quadrature(self, maps_q, out=None):
+        """Integrals over the sphere (Sec. IV-F) of the batch of maps in the
+        quadrature layout [batch][L(L-1)+1] (CUDA complex128); returns [batch]."""
+        n = self.batch * quadrature_size(self.L)
+        if maps_q.dtype != torch.complex128 or not maps_q.is_cuda or maps_q.numel() != n:
+            raise ValueError(f"expected a complex128 CUDA tensor of {n} elements")
+        maps_q = maps_q.contiguous()
+        if out is None:
+            out = torch.empty(self.batch, dtype=torch.complex128, device=maps_q.device)
+        st = lib().mw_quadrature(self._h, ctypes.c_void_p(maps_q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 _stream_of(maps_q))
+        if st != MW_OK:
+            raise MWError(st, "mw_quadrature")
+        return out
 
     def forward_adjoint(self, flm, out=None):
         return self._call("mw_forward_adjoint", flm, self._nflm, self._nmap, out)
