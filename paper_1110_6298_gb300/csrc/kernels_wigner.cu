@@ -112,12 +112,14 @@ __device__ __forceinline__ double prev_val(const double* __restrict__ d, int LD,
 __device__ __forceinline__ int tile_index(int I, int J) { return I * (I + 1) / 2 + J; }
 
 // Wait until tile t has published step `step` (bounded; returns false on timeout).
+// The first polls spin (a neighbour of the same wavefront is usually about to
+// publish); later ones back off with a short sleep.
 __device__ __forceinline__ bool wait_tile(const int* prog, int t, int step) {
   for (unsigned polls = 0; polls < kBarrierPolls; ++polls) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(prog + t) : "memory");
     if (v >= step) return true;
-    __nanosleep(32);
+    if (polls >= 256) __nanosleep(32);
   }
   return false;
 }
