@@ -475,6 +475,75 @@ def quadrature_samples(flm, L, s):
 
 
 # --------------------------------------------------------------------------
+# Real spin-0 signals (Sec. IV-G)
+# --------------------------------------------------------------------------
+
+def _neg_m_sign(L):
+    """(-1)^m of every packed index l*l + l + m."""
+    m = np.concatenate([np.arange(-l, l + 1) for l in range(L)])
+    return np.where(m % 2 == 0, 1.0, -1.0)
+
+
+def _mirror_index(L):
+    """Packed index of (l, -m) for every packed index of (l, m)."""
+    return np.concatenate([l * l + l - np.arange(-l, l + 1) for l in range(L)])
+
+
+def fill_negative_m(flm, L):
+    """Complete coefficients known for m >= 0 with the reality condition of a
+    real scalar signal (Sec. IV-G): f_{l,-m} = (-1)^m conj(f_lm)."""
+    flm = np.array(flm, dtype=np.complex128)
+    pos = np.concatenate([l * l + l + np.arange(0, l + 1) for l in range(L)])
+    neg = _mirror_index(L)[pos]
+    flm[..., neg] = _neg_m_sign(L)[pos] * np.conj(flm[..., pos])
+    return flm
+
+
+def hermitian_part(flm, L):
+    """Coefficients of Re(f) for a scalar signal f with coefficients f_lm:
+    conj(f) has coefficients (-1)^m conj(f_{l,-m}) (the relation behind the
+    reality condition of Sec. IV-G), so Re(f) has
+    (f_lm + (-1)^m conj(f_{l,-m})) / 2."""
+    flm = np.asarray(flm, dtype=np.complex128)
+    return 0.5 * (flm + _neg_m_sign(L) * np.conj(flm[..., _mirror_index(L)]))
+
+
+def forward_real(f_map, L):
+    """Forward transform of real scalar maps (Sec. IV-G): only m >= 0 is
+    evaluated through the phi DFT, extension, theta DFT, convolution and Wigner
+    stage (each m is independent until the end), and m < 0 follows from the
+    reality condition.  f_map: real [N_MW] or [B, N_MW]."""
+    f_map = np.asarray(f_map)
+    if np.iscomplexobj(f_map):
+        raise TypeError("forward_real takes real maps")
+    half = forward(f_map.astype(np.complex128), L, 0, m_list=range(0, L))
+    return fill_negative_m(half, L)
+
+
+def inverse_real(flm, L):
+    """Real part of the inverse transform of scalar coefficients (Sec. IV-G):
+    the inverse of their Hermitian part.  For those F_{-m,-m'} = conj(F_mm'),
+    so only the rows m >= 0 go through the theta synthesis (Eq. Fmt), and the
+    phi synthesis (Eq. f_pfft) is the real inverse DFT of F_m(theta_t),
+    m = 0..L-1.  flm: [L*L] or [B, L*L]; returns real maps."""
+    _check(L, 0)
+    flm = np.asarray(flm, dtype=np.complex128)
+    single = flm.ndim == 1
+    h = hermitian_part(flm[None] if single else flm, L)
+    M = 2 * L - 1
+    outs = []
+    for F in inverse_wigner(h, L, 0):
+        F_mt = theta_synthesis(F[L - 1:], L)             # [t, m >= 0]
+        rings = sfft.irfft(F_mt, n=M, axis=1) * M        # F_0 + 2 Re sum_{m>0} F_m e^{i m phi_p}
+        out = np.empty(sample_count(L), dtype=np.float64)
+        out[: (L - 1) * M] = rings[: L - 1].reshape(-1)
+        out[(L - 1) * M] = rings[L - 1, 0]
+        outs.append(out)
+    out = np.stack(outs)
+    return out[0] if single else out
+
+
+# --------------------------------------------------------------------------
 # Error measures (relative max and relative RMS, plus the paper's max-abs)
 # --------------------------------------------------------------------------
 

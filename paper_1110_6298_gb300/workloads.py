@@ -51,6 +51,26 @@ def uniform_flm(g: np.random.Generator, L: int, s: int) -> np.ndarray:
     return np.where(ell < abs(s), 0, x)
 
 
+def uniform_flm_real(g: np.random.Generator, L: int) -> np.ndarray:
+    """Coefficients of a real scalar signal: one complex draw per packed index
+    (Re, Im uniform on [-1, 1], as uniform_flm), then the m = 0 entries keep
+    their real part and each entry m < 0 is laid out as (-1)^m times the
+    conjugate of the entry at +m, the structure the reality condition of
+    Sec. IV-G fixes."""
+    x = g.uniform(-1, 1, L * L) + 1j * g.uniform(-1, 1, L * L)
+    ell = ell_of_index(L)
+    m = np.arange(L * L) - ell * ell - ell
+    mirror = ell * ell + ell - m
+    sign = np.where(m % 2 == 0, 1.0, -1.0)
+    out = np.where(m > 0, x, np.where(m == 0, x.real + 0j, sign * np.conj(x[mirror])))
+    return out
+
+
+def gaussian_real_map(g: np.random.Generator, L: int) -> np.ndarray:
+    """I.i.d. real N(0, 1) samples on every grid point."""
+    return g.standard_normal(map_size(L))
+
+
 def gaussian_map(g: np.random.Generator, L: int) -> np.ndarray:
     """I.i.d. complex N(0, 1) samples (Re, Im ~ N(0, 1/2)) on every grid point."""
     n = map_size(L)
