@@ -81,6 +81,24 @@ enum { MW_PREC_FP64 = 0, MW_PREC_MIXED = 1, MW_PREC_MIXED_BF16X3 = 1, MW_PREC_MI
  * on; if capture is not possible the plan runs its calls directly. */
 enum { MW_FLAG_GRAPH = 1 << 8 };
 
+/* MW_FLAG_REAL (or-ed into flags): real scalar signals (Sec. IV-G).  Every spin
+ * must be 0 and `batch` counts real maps.  Map buffers hold real doubles,
+ * [batch][N_MW]; f_lm buffers stay complex doubles [batch][L*L] with every m.
+ *   mw_forward writes coefficients that satisfy the reality condition
+ *     f_{l,-m} = (-1)^m conj(f_lm) exactly (m < 0 mirrors m > 0; f_l0 real).
+ *   mw_inverse returns the real part of the synthesis of the given
+ *     coefficients, which is the synthesis itself when they satisfy the
+ *     reality condition.
+ *   mw_forward_inverse: both, sharing the recursion as on complex plans.
+ * The transforms pair the maps: maps 2b and 2b+1 travel as the real and
+ * imaginary part of one complex spin-0 map and are separated with the reality
+ * condition, so a real plan of `batch` maps costs a complex plan of
+ * (batch + 1) / 2 maps plus one O(L^2) pass over the coefficients (the paper
+ * halves the m range per map instead; the factor of two is the same).
+ * Adjoints and mw_quadrature return MW_EUNSUPPORTED on real plans; ragged
+ * plans reject the flag (MW_EINVAL). */
+enum { MW_FLAG_REAL = 1 << 9 };
+
 /* Create a plan for `batch` maps of band limit L and spin s.
  * Requires 1 <= L <= 2048, |s| < L, batch >= 1, out != NULL.  Allocates the
  * device workspace on the current CUDA device; *out is NULL on failure. */
@@ -98,7 +116,8 @@ mw_status mw_plan_create_spins(mw_plan **out, int L, int batch, const int *spins
  * serves every map (Delta^l depends on neither L nor s). */
 mw_status mw_plan_create_ragged(mw_plan **out, int n, const int *L, const int *spins, unsigned flags);
 
-/* Total complex elements of the plan's map buffer and f_lm buffer. */
+/* Total elements of the plan's map buffer and f_lm buffer (complex doubles;
+ * the map buffer of a MW_FLAG_REAL plan counts real doubles). */
 size_t mw_plan_map_elems(const mw_plan *plan);
 size_t mw_plan_flm_elems(const mw_plan *plan);
 
@@ -179,7 +198,8 @@ int mw_plan_last_launches(const mw_plan *plan);
 
 /* Per-stage timing (diagnostics, not in the paper).  With timing enabled, each
  * call records CUDA events on its stream around every stage:
- *   MW_STAGE_PHI     phi DFTs (and their adjoints)
+ *   MW_STAGE_PHI     phi DFTs (and their adjoints); on real plans also the
+ *                    f_lm pack / unpack of the map pairs
  *   MW_STAGE_THETA   theta extension / DFT / weight convolution (and adjoints)
  *   MW_STAGE_DELTA   Risbo recursion of the Wigner-Delta planes
  *   MW_STAGE_CONTRACT Delta contraction (forward or inverse sum)

@@ -33,6 +33,11 @@ struct mw_plan {
   int prec = MW_PREC_FP64;
   int device = 0;
   std::vector<int> spins;          // per map
+  // real-signal plans (MW_FLAG_REAL): nreal real spin-0 maps packed two per
+  // complex map, so B = (nreal + 1) / 2; d_gpack holds the packed f_lm [B][L*L]
+  bool real = false;
+  int nreal = 0;
+  double2* d_gpack = nullptr;
   // caller-buffer offsets (complex elements) of each map and f_lm block
   std::vector<long long> moff, foff;
   long long* d_moff = nullptr;
@@ -126,6 +131,11 @@ cudaError_t launch_flm_to_f32(const mw_plan* p, const double2* flm, cudaStream_t
 cudaError_t launch_dmma_forward(const mw_plan* p, int l0, int l1, double2* flm, cudaStream_t st);
 cudaError_t launch_dmma_inverse(const mw_plan* p, int l0, int l1, const double2* flm, cudaStream_t st);
 cudaError_t launch_phi_inverse_adjoint(const mw_plan* p, const double2* map, cudaStream_t st);
+// real-signal plans: phi stages on pairs of real maps, and the f_lm pack/unpack
+cudaError_t launch_phi_forward_real(const mw_plan* p, const double* maps, cudaStream_t st);
+cudaError_t launch_phi_inverse_real(const mw_plan* p, double* maps, cudaStream_t st);
+cudaError_t launch_real_unpack(const mw_plan* p, const double2* g, double2* flm, cudaStream_t st);
+cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, cudaStream_t st);
 
 // Wigner stage: one sweep l = 0..o->L-1 with Risbo's recursion (state of the
 // owner o) and the contractions of the consumer plans cs[0..nc).

@@ -81,34 +81,63 @@ __device__ __forceinline__ C<T> mul_ipow(C<T> x, int k) {
 struct Dims {
   int L, M, N, B;
   long long nmw;  // samples per map
+  int nreal;      // real-signal plans: real maps in the caller's buffer (map b packs maps 2b, 2b+1)
 };
+
+// Sample i of map b.  Complex plans: the caller's complex map at moff[b].
+// Real-signal plans: real maps 2b and 2b+1 (back to back, nmw doubles each) as
+// the real and imaginary part; the second is zero past the last real map.
+template <typename T, bool RealIo>
+__device__ __forceinline__ C<T> load_sample(const void* __restrict__ map, const long long* __restrict__ moff,
+                                            const Dims& d, int b, long long i) {
+  if constexpr (RealIo) {
+    const double* fr = static_cast<const double*>(map) + (long long)(2 * b) * d.nmw;
+    const double im = (2 * b + 1 < d.nreal) ? fr[d.nmw + i] : 0.0;
+    return mkc<T>((T)fr[i], (T)im);
+  } else {
+    return from64<T>(static_cast<const double2*>(map)[moff[b] + i]);
+  }
+}
+
+// Store sample i of map b (the inverse of load_sample's layout; real-signal
+// plans keep the real part in map 2b and the imaginary part in map 2b+1).
+template <typename T, bool RealIo>
+__device__ __forceinline__ void store_sample(void* __restrict__ map, const long long* __restrict__ moff, const Dims& d,
+                                             int b, long long i, C<T> v) {
+  if constexpr (RealIo) {
+    double* fr = static_cast<double*>(map) + (long long)(2 * b) * d.nmw;
+    fr[i] = (double)v.x;
+    if (2 * b + 1 < d.nreal) fr[d.nmw + i] = (double)v.y;
+  } else {
+    static_cast<double2*>(map)[moff[b] + i] = make_double2((double)v.x, (double)v.y);
+  }
+}
 
 __device__ __forceinline__ int spin_of(const int* spins, int b) { return spins[b]; }
 
 // --------------------------------------------------------------------------
 // forward
 // --------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const double2* __restrict__ map,
+template <typename T, bool RealIo>
+__global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const void* __restrict__ map,
                               const long long* __restrict__ moff,
                               C<T>* __restrict__ Gt /* [B][M][L] */, const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int t = blockIdx.x, b = blockIdx.y;
   const int L = d.L, M = d.M;
-  const double2* f = map + moff[b];
   C<T>* out = Gt + (long long)b * M * L;
   if (t == L - 1) {  // pole ring: 2 pi f(pi,0) delta_{m,s}
     const int s = spin_of(spins, b);
-    const double2 fp = f[(long long)(L - 1) * M];
+    const C<T> fp = load_sample<T, RealIo>(map, moff, d, b, (long long)(L - 1) * M);
     const T tp = (T)(2.0 * M_PI);
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       const int m = i - (L - 1);
-      out[(long long)i * L + t] = (m == s) ? mkc<T>((T)fp.x * tp, (T)fp.y * tp) : mkc<T>(0, 0);
+      out[(long long)i * L + t] = (m == s) ? mkc<T>(fp.x * tp, fp.y * tp) : mkc<T>(0, 0);
     }
     return;
   }
-  for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = from64<T>(f[(long long)t * M + p]);
+  for (int p = threadIdx.x; p < M; p += blockDim.x) buf[p] = load_sample<T, RealIo>(map, moff, d, b, (long long)t * M + p);
   __syncthreads();
   const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, false);
   const T sc = (T)(2.0 * M_PI / M);
@@ -218,9 +247,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_theta_inverse(Dims d, FftDes
   for (int t = threadIdx.x; t < L; t += blockDim.x) out[(long long)t * M + im] = res[t];
 }
 
-template <typename T>
+template <typename T, bool RealIo>
 __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc fM, const C<T>* __restrict__ twM, const C<T>* __restrict__ Gt,
-                              double2* __restrict__ map, const long long* __restrict__ moff) {
+                              void* __restrict__ map, const long long* __restrict__ moff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
   const int L = d.L, M = d.M;
@@ -232,11 +261,10 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_inverse(Dims d, FftDesc 
   }
   __syncthreads();
   const C<T>* res = fft_pp<T>(buf, buf + M, fM, twM, true);
-  double2* f = map + moff[b];
   if (t < L - 1) {
-    for (int p = threadIdx.x; p < M; p += blockDim.x) f[(long long)t * M + p] = to64(res[p]);
+    for (int p = threadIdx.x; p < M; p += blockDim.x) store_sample<T, RealIo>(map, moff, d, b, (long long)t * M + p, res[p]);
   } else if (threadIdx.x == 0) {
-    f[(long long)(L - 1) * M] = to64(res[0]);
+    store_sample<T, RealIo>(map, moff, d, b, (long long)(L - 1) * M, res[0]);
   }
 }
 
@@ -453,6 +481,7 @@ Dims dims_of(const mw_plan* p) {
   Dims d;
   d.L = p->L; d.M = p->M; d.N = p->N; d.B = p->B;
   d.nmw = (long long)(p->L - 1) * p->M + 1;
+  d.nreal = p->real ? p->nreal : 0;
   return d;
 }
 
@@ -472,12 +501,12 @@ constexpr int kSmemMax = 232448;
 
 template <typename T> int pp_bytes(int n) { return 2 * n * (int)sizeof(C<T>); }
 
-template <typename T>
-cudaError_t phi_forward_t(const mw_plan* p, const double2* map, cudaStream_t st) {
+template <typename T, bool RealIo>
+cudaError_t phi_forward_t(const mw_plan* p, const void* map, cudaStream_t st) {
   const int sm = pp_bytes<T>(p->M);
-  cudaError_t e = set_smem(k_phi_forward<T>, sm);
+  cudaError_t e = set_smem(k_phi_forward<T, RealIo>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_forward<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
+  k_phi_forward<T, RealIo><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, map, p->d_moff, (C<T>*)p->d_Gt, p->d_spins);
   return cudaGetLastError();
 }
@@ -508,12 +537,12 @@ cudaError_t theta_inverse_t(const mw_plan* p, cudaStream_t st) {
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_phase, p->d_Gp, (C<T>*)p->d_Gt, p->d_spins);
   return cudaGetLastError();
 }
-template <typename T>
-cudaError_t phi_inverse_t(const mw_plan* p, double2* map, cudaStream_t st) {
+template <typename T, bool RealIo>
+cudaError_t phi_inverse_t(const mw_plan* p, void* map, cudaStream_t st) {
   const int sm = pp_bytes<T>(p->M);
-  cudaError_t e = set_smem(k_phi_inverse<T>, sm);
+  cudaError_t e = set_smem(k_phi_inverse<T, RealIo>, sm);
   if (e != cudaSuccess) return e;
-  k_phi_inverse<T><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
+  k_phi_inverse<T, RealIo><<<dim3(p->L, p->B), threads_pp(p->M), sm, st>>>(
       dims_of(p), p->fM, (const C<T>*)p->d_twM, (const C<T>*)p->d_Gt, map, p->d_moff);
   return cudaGetLastError();
 }
@@ -568,13 +597,22 @@ cudaError_t theta_inverse_adjoint_t(const mw_plan* p, cudaStream_t st) {
 
 #define DISPATCH(p, fn, ...) ((p)->prec == MW_PREC_FP64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
 
+#define DISPATCH2(p, fn, R, ...) \
+  ((p)->prec == MW_PREC_FP64 ? fn<double, R>(__VA_ARGS__) : fn<float, R>(__VA_ARGS__))
+
 cudaError_t launch_phi_forward(const mw_plan* p, const double2* map, cudaStream_t st) {
-  return DISPATCH(p, phi_forward_t, p, map, st);
+  return DISPATCH2(p, phi_forward_t, false, p, map, st);
+}
+cudaError_t launch_phi_forward_real(const mw_plan* p, const double* maps, cudaStream_t st) {
+  return DISPATCH2(p, phi_forward_t, true, p, maps, st);
+}
+cudaError_t launch_phi_inverse_real(const mw_plan* p, double* maps, cudaStream_t st) {
+  return DISPATCH2(p, phi_inverse_t, true, p, maps, st);
 }
 cudaError_t launch_theta_forward(const mw_plan* p, cudaStream_t st) { return DISPATCH(p, theta_forward_t, p, st); }
 cudaError_t launch_theta_inverse(const mw_plan* p, cudaStream_t st) { return DISPATCH(p, theta_inverse_t, p, st); }
 cudaError_t launch_phi_inverse(const mw_plan* p, double2* map, cudaStream_t st) {
-  return DISPATCH(p, phi_inverse_t, p, map, st);
+  return DISPATCH2(p, phi_inverse_t, false, p, map, st);
 }
 cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st) {
   return DISPATCH(p, theta_forward_adjoint_t, p, st);

@@ -74,7 +74,7 @@ void free_plan(mw_plan* p) {
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
-                  p->d_qw,     p->d_qpart};
+                  p->d_qw,     p->d_qpart, p->d_gpack};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -101,9 +101,21 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   if (L < 1 || L > 2048 || B < 1 || !spins) return MW_EINVAL;
   const int prec = (int)(flags & 0xffu);
   if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED && prec != MW_PREC_MIXED_TF32X3) return MW_EINVAL;
-  if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH)) return MW_EINVAL;
+  if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH | (unsigned)MW_FLAG_REAL)) return MW_EINVAL;
   for (int b = 0; b < B; ++b)
     if (spins[b] <= -L || spins[b] >= L) return MW_EINVAL;
+  // real-signal plans: spin 0 only, caller-contiguous buffers, two real maps per complex map
+  const bool real = (flags & MW_FLAG_REAL) != 0;
+  const int nreal = B;
+  std::vector<int> zeros;
+  if (real) {
+    if (moff || foff || sweep_only) return MW_EINVAL;
+    for (int b = 0; b < B; ++b)
+      if (spins[b] != 0) return MW_EINVAL;
+    B = (B + 1) / 2;
+    zeros.assign(B, 0);
+    spins = zeros.data();
+  }
 
   mw_plan* p = new (std::nothrow) mw_plan();
   if (!p) return MW_ENOMEM;
@@ -127,6 +139,12 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   }
   p->map_elems = (long long)B * nmw;
   p->flm_elems = (long long)B * L * L;
+  if (real) {  // caller-facing sizes: nreal real maps and nreal f_lm blocks
+    p->real = true;
+    p->nreal = nreal;
+    p->map_elems = (long long)nreal * nmw;
+    p->flm_elems = (long long)nreal * L * L;
+  }
   if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
 
   // spin groups (order of first appearance; at most kMaxGroupMaps maps each,
@@ -252,6 +270,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     alloc(&p->d_Gt, fsz * (size_t)B * M * L);
     alloc((void**)&p->d_Gp, sizeof(double2) * (size_t)B * M * L);
     if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
+    if (real) alloc((void**)&p->d_gpack, sizeof(double2) * (size_t)B * L * L);
   }
   if (owner) {  // borrow the parent's sweep state
     p->shared_sweep = true;
@@ -309,7 +328,9 @@ mw_status ensure_twins(mw_plan* p) {
   else src = p->subs;
   for (mw_plan* q : src) {
     mw_plan* t = nullptr;
-    const mw_status st = build_plan(&t, q->L, q->B, q->spins.data(), q->flags, q->moff.data(), q->foff.data(), p, false);
+    const mw_status st =
+        q->real ? build_plan(&t, q->L, q->nreal, std::vector<int>(q->nreal, 0).data(), q->flags, nullptr, nullptr, p)
+                : build_plan(&t, q->L, q->B, q->spins.data(), q->flags, q->moff.data(), q->foff.data(), p, false);
     if (st != MW_OK) {
       for (mw_plan* u : p->twins) {
         p->ws_bytes -= u->ws_bytes;
@@ -341,14 +362,18 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   std::vector<mw_plan*> cs;
   if (p->subs.empty()) cs.push_back(p);
   else cs = p->subs;
-  const size_t nmw = (size_t)p->map_elems, nlm = (size_t)p->flm_elems;
+  const bool real = p->real;
+  if (real && (dir == kForwardAdjoint || dir == kInverseAdjoint)) return MW_EUNSUPPORTED;
+  // buffer sizes in bytes: complex doubles, or real doubles for the maps of a real plan
+  const size_t nmw = (size_t)p->map_elems * (real ? sizeof(double) : sizeof(double2));
+  const size_t nlm = (size_t)p->flm_elems * sizeof(double2);
   const bool map_in = (dir == kForward || dir == kInverseAdjoint || fused);
-  const size_t in_elems = map_in ? nmw : nlm, out_elems = map_in ? nlm : nmw;
+  const size_t in_bytes = map_in ? nmw : nlm, out_bytes = map_in ? nlm : nmw;
   cudaError_t e = cudaSuccess;
-  auto ensure = [&](double2** slot, size_t elems) {
+  auto ensure = [&](double2** slot, size_t bytes) {
     if (e != cudaSuccess || *slot) return;
-    e = cudaMalloc((void**)slot, sizeof(double2) * elems);
-    if (e == cudaSuccess) p->ws_bytes += sizeof(double2) * elems;
+    e = cudaMalloc((void**)slot, bytes);
+    if (e == cudaSuccess) p->ws_bytes += bytes;
   };
   // host buffers are staged through plan-owned device buffers (allocated on first use)
   const double2* din = (const double2*)in;
@@ -359,18 +384,18 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   double2** out_slot = map_in ? &p->d_flm_stage : &p->d_map_stage;
   const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
   const bool in2_dev = !fused || is_device_ptr(in2), out2_dev = !fused || is_device_ptr(out2);
-  if (!in_dev) ensure(in_slot, in_elems);
-  if (!out_dev) ensure(out_slot, out_elems);
+  if (!in_dev) ensure(in_slot, in_bytes);
+  if (!out_dev) ensure(out_slot, out_bytes);
   if (!in2_dev) ensure(&p->d_flm_stage2, nlm);
   if (!out2_dev) ensure(&p->d_map_stage2, nmw);
   if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
   if (!in_dev) {
-    e = cudaMemcpyAsync(*in_slot, in, sizeof(double2) * in_elems, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(*in_slot, in, in_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
     din = *in_slot;
   }
   if (!in2_dev) {
-    e = cudaMemcpyAsync(p->d_flm_stage2, in2, sizeof(double2) * nlm, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(p->d_flm_stage2, in2, nlm, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
     din2 = p->d_flm_stage2;
   }
@@ -407,6 +432,52 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
     e = run_wigner(p, jobs.data(), (int)jobs.size(), st, &nl);
   };
   const std::vector<mw_plan*> none;
+  // real plans: f_lm pack (caller -> packed workspace) and unpack (packed -> caller)
+  auto pack = [&](mw_plan* c, const double2* flm) {
+    if (e != cudaSuccess) return;
+    StageSpan sp(p, MW_STAGE_PHI, st);
+    e = launch_real_pack(c, flm, c->d_gpack, st);
+    ++nl;
+    sp.end(1);
+  };
+  auto unpack = [&](mw_plan* c, double2* flm) {
+    if (e != cudaSuccess) return;
+    StageSpan sp(p, MW_STAGE_PHI, st);
+    e = launch_real_unpack(c, c->d_gpack, flm, st);
+    ++nl;
+    sp.end(1);
+  };
+  if (real) {  // one consumer (no ragged real plans)
+    mw_plan* c = cs[0];
+    switch (dir) {
+      case kForward:
+        phi(cs, launch_phi_forward_real, (const double*)din);
+        stage(cs, MW_STAGE_THETA, launch_theta_forward);
+        wigner(cs, c->d_gpack, none, nullptr);
+        unpack(c, dout);
+        break;
+      case kInverse:
+        pack(c, din);
+        wigner(none, nullptr, cs, c->d_gpack);
+        stage(cs, MW_STAGE_THETA, launch_theta_inverse);
+        phi(cs, launch_phi_inverse_real, (double*)dout);
+        break;
+      case kFused: {
+        mw_plan* t = p->twins[0];
+        phi(cs, launch_phi_forward_real, (const double*)din);
+        stage(cs, MW_STAGE_THETA, launch_theta_forward);
+        pack(t, din2);
+        wigner(cs, c->d_gpack, p->twins, t->d_gpack);
+        unpack(c, dout);
+        stage(p->twins, MW_STAGE_THETA, launch_theta_inverse);
+        phi(p->twins, launch_phi_inverse_real, (double*)dout2);
+        break;
+      }
+      default:
+        break;
+    }
+    return e;
+  }
   switch (dir) {
     case kForward:
       phi(cs, launch_phi_forward, din);
@@ -492,9 +563,8 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   }
   if (e != cudaSuccess) return from_cuda(e);
   if (!out_dev || !out2_dev) {
-    if (!out_dev) e = cudaMemcpyAsync(out, dout, sizeof(double2) * out_elems, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && !out2_dev)
-      e = cudaMemcpyAsync(out2, dout2, sizeof(double2) * nmw, cudaMemcpyDeviceToHost, st);
+    if (!out_dev) e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !out2_dev) e = cudaMemcpyAsync(out2, dout2, nmw, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
   }
@@ -509,7 +579,7 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
 mw_status build_ragged(mw_plan** out, int n, const int* Ls, const int* spins, unsigned flags) {
   if (!out) return MW_EINVAL;
   *out = nullptr;
-  if (n < 1 || n > (1 << 20) || !Ls || !spins) return MW_EINVAL;
+  if (n < 1 || n > (1 << 20) || !Ls || !spins || (flags & MW_FLAG_REAL)) return MW_EINVAL;
   int Lmax = 0;
   std::vector<long long> moff(n), foff(n);
   long long mo = 0, fo = 0;
@@ -668,7 +738,7 @@ mw_status mw_quadrature_weights(int L, int s, double* q_out, void* stream) {
 
 mw_status mw_quadrature(mw_plan* plan, const void* maps_q, void* integrals, void* stream) {
   if (!plan || !maps_q || !integrals) return MW_EINVAL;
-  if (!plan->subs.empty()) return MW_EUNSUPPORTED;
+  if (!plan->subs.empty() || plan->real) return MW_EUNSUPPORTED;
   if (!is_device_ptr(maps_q) || !is_device_ptr(integrals)) return MW_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmw.so")
 MW_OK, MW_EINVAL, MW_ENOMEM, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = range(6)
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_bf16": 1, "mixed_tf32": 2}
 FLAG_GRAPH = 1 << 8
+FLAG_REAL = 1 << 9
 
 _lib = None
 
@@ -254,6 +255,86 @@ class Plan:
 
     def inverse_adjoint(self, maps, out=None):
         return self._call("mw_inverse_adjoint", maps, self._nmap, self._nflm, out)
+
+
+class RealPlan(Plan):
+    """`batch` real scalar maps (Sec. IV-G): maps are float64 [batch][N_MW],
+    coefficients complex128 [batch][L*L].
+
+    forward returns coefficients that satisfy f_{l,-m} = (-1)^m conj(f_lm)
+    exactly; inverse returns the real part of the synthesis of the given
+    coefficients.  The library carries two real maps per complex transform, so
+    a batch of B real maps costs a complex batch of ceil(B/2).  No adjoints or
+    quadrature on real plans."""
+
+    def __init__(self, L, batch=1, precision="fp64", graph=False):
+        self.L, self.batch, self.spins = int(L), int(batch), [0] * int(batch)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        flags = PRECISIONS[precision] | FLAG_REAL | (FLAG_GRAPH if graph else 0)
+        st = lib().mw_plan_create(ctypes.byref(h), self.L, 0, self.batch, flags)
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_create (real)")
+        self._h = h
+        self._nmap = self.batch * map_size(self.L)
+        self._nflm = self.batch * flm_size(self.L)
+
+    def _rcall(self, name, x, in_dtype, n_in, out_dtype, n_out, out):
+        if x.dtype != in_dtype:
+            raise TypeError(f"expected a {in_dtype} tensor")
+        if x.numel() != n_in:
+            raise ValueError(f"expected {n_in} elements, got {tuple(x.shape)}")
+        x = x.contiguous()
+        if out is None:
+            out = torch.empty((self.batch, n_out // self.batch), dtype=out_dtype, device=x.device)
+        elif out.dtype != out_dtype or out.numel() != n_out or not out.is_contiguous():
+            raise ValueError("bad output tensor")
+        st = getattr(lib(), name)(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  _stream_of(x))
+        if st != MW_OK:
+            raise MWError(st, name)
+        return out
+
+    def forward(self, maps, out=None):
+        return self._rcall("mw_forward", maps, torch.float64, self._nmap, torch.complex128, self._nflm, out)
+
+    def inverse(self, flm, out=None):
+        return self._rcall("mw_inverse", flm, torch.complex128, self._nflm, torch.float64, self._nmap, out)
+
+    def forward_inverse(self, maps, flm, flm_out=None, map_out=None):
+        """Forward of the real `maps` and inverse of `flm` sharing one
+        Wigner-Delta recursion; returns (flm_out, map_out)."""
+        for x, dt, n in ((maps, torch.float64, self._nmap), (flm, torch.complex128, self._nflm)):
+            if x.dtype != dt:
+                raise TypeError(f"expected {dt}")
+            if x.numel() != n:
+                raise ValueError(f"expected {n} elements, got {tuple(x.shape)}")
+        maps, flm = maps.contiguous(), flm.contiguous()
+
+        def make(o, n, dt, like):
+            if o is None:
+                return torch.empty((self.batch, n // self.batch), dtype=dt, device=like.device)
+            if o.dtype != dt or o.numel() != n or not o.is_contiguous():
+                raise ValueError("bad output tensor")
+            return o
+
+        flm_out = make(flm_out, self._nflm, torch.complex128, maps)
+        map_out = make(map_out, self._nmap, torch.float64, flm)
+        st = lib().mw_forward_inverse(self._h, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(flm_out.data_ptr()),
+                                      ctypes.c_void_p(flm.data_ptr()), ctypes.c_void_p(map_out.data_ptr()),
+                                      _stream_of(maps))
+        if st != MW_OK:
+            raise MWError(st, "mw_forward_inverse")
+        return flm_out, map_out
+
+    def forward_adjoint(self, flm, out=None):
+        raise MWError(MW_EUNSUPPORTED, "forward_adjoint on a real plan")
+
+    def inverse_adjoint(self, maps, out=None):
+        raise MWError(MW_EUNSUPPORTED, "inverse_adjoint on a real plan")
+
+    def quadrature(self, maps_q, out=None):
+        raise MWError(MW_EUNSUPPORTED, "quadrature on a real plan")
 
 
 class RaggedPlan(Plan):

@@ -1,0 +1,195 @@
+"""GPU parity of real-signal plans (Sec. IV-G) through the C ABI against the
+oracle's real-signal transforms.
+
+Tolerances as for complex plans (relative max error): 1e-12 FP64, 1e-6 mixed.
+Besides the values, the forward's output must satisfy the reality condition
+f_{l,-m} = (-1)^m conj(f_lm) bit for bit (f_l0 real), because the unpack forms
+each (l, m), (l, -m) pair from one set of reads.  Batches cover an even count,
+an odd count (the last map pairs with a zero imaginary part) and one map; sizes
+span several 32-wide recursion tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1110_6298_gb300 import workloads as wl  # noqa: E402
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "mixed_tf32": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def mw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_6298_gb300 import build
+    build.build()
+    from paper_1110_6298_gb300 import mw as m
+    m.lib()
+    return m
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def real_maps(L, n, seed):
+    g = wl.rng(3000 + seed)
+    return np.stack([wl.gaussian_real_map(g, L) for _ in range(n)])
+
+
+def any_flm(L, n, seed):
+    g = wl.rng(3100 + seed)
+    return np.stack([wl.uniform_flm(g, L, 0) for _ in range(n)])
+
+
+def mirror_ok(flm, L):
+    """Bitwise f_{l,-m} == (-1)^m conj(f_lm) and Im f_l0 == 0 on a [B, L*L] tensor."""
+    ell = wl.ell_of_index(L)
+    m = np.arange(L * L) - ell * ell - ell
+    pos = np.nonzero(m > 0)[0]
+    neg = ell[pos] ** 2 + ell[pos] - m[pos]
+    sign = torch.from_numpy(np.where(m[pos] % 2 == 0, 1.0, -1.0)).to(flm.device)
+    a = flm[:, torch.from_numpy(pos).to(flm.device)]
+    b = flm[:, torch.from_numpy(neg).to(flm.device)]
+    z = flm[:, torch.from_numpy(np.nonzero(m == 0)[0]).to(flm.device)]
+    return bool(torch.equal(b, sign * a.conj())) and bool(torch.all(z.imag == 0))
+
+
+CASES = [(1, 1), (2, 3), (5, 2), (33, 4), (65, 3), (130, 1), (200, 5)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tf32"])
+@pytest.mark.parametrize("L,B", CASES)
+def test_forward(mw, prec, L, B):
+    x = real_maps(L, B, L + B)
+    plan = mw.RealPlan(L, B, precision=prec)
+    f = plan.forward(torch.from_numpy(x).cuda())
+    plan.sync()
+    assert f.dtype == torch.complex128 and f.shape == (B, L * L)
+    assert mirror_ok(f, L)
+    ref = oracle.forward_real(x, L)
+    for b in range(B):
+        assert relmax(f[b].cpu().numpy(), ref[b]) < TOL[prec], b
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_tf32"])
+@pytest.mark.parametrize("L,B", CASES)
+def test_inverse(mw, prec, L, B):
+    c = any_flm(L, B, L + B)  # not Hermitian: the result is the real part of the synthesis
+    plan = mw.RealPlan(L, B, precision=prec)
+    x = plan.inverse(torch.from_numpy(c).cuda())
+    plan.sync()
+    assert x.dtype == torch.float64 and x.shape == (B, wl.map_size(L))
+    ref = oracle.inverse_real(c, L)
+    for b in range(B):
+        assert relmax(x[b].cpu().numpy(), ref[b]) < TOL[prec], b
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_round_trip(mw, prec):
+    L, B = 96, 3
+    c = np.stack([wl.uniform_flm_real(wl.rng(3200 + b), L) for b in range(B)])
+    plan = mw.RealPlan(L, B, precision=prec)
+    back = plan.forward(plan.inverse(torch.from_numpy(c).cuda()))
+    plan.sync()
+    assert relmax(back.cpu().numpy(), c) < (1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fused_equals_separate(mw, prec):
+    L, B = 70, 5
+    x = torch.from_numpy(real_maps(L, B, 1)).cuda()
+    c = torch.from_numpy(any_flm(L, B, 1)).cuda()
+    plan = mw.RealPlan(L, B, precision=prec)
+    f_sep, m_sep = plan.forward(x), plan.inverse(c)
+    f_fu, m_fu = plan.forward_inverse(x, c)
+    f2, m2 = plan.forward_inverse(x, c)
+    plan.sync()
+    assert torch.equal(f_fu, f_sep) and torch.equal(m_fu, m_sep)
+    assert torch.equal(f2, f_sep) and torch.equal(m2, m_sep)
+
+
+def test_host_buffers_and_graph(mw):
+    L, B = 48, 3
+    x = torch.from_numpy(real_maps(L, B, 2))
+    c = torch.from_numpy(any_flm(L, B, 2))
+    ref = mw.RealPlan(L, B, precision="mixed")
+    f_dev = ref.forward(x.cuda())
+    m_dev = ref.inverse(c.cuda())
+    ref.sync()
+    host = mw.RealPlan(L, B, precision="mixed")
+    assert torch.equal(host.forward(x), f_dev.cpu())
+    assert torch.equal(host.inverse(c), m_dev.cpu())
+    g = mw.RealPlan(L, B, precision="mixed", graph=True)
+    xd, cd = x.cuda(), c.cuda()
+    fo = torch.empty_like(f_dev)
+    mo = torch.empty_like(m_dev)
+    for _ in range(2):
+        g.forward(xd, out=fo)
+        g.inverse(cd, out=mo)
+        g.sync()
+        assert torch.equal(fo, f_dev) and torch.equal(mo, m_dev)
+    assert g.last_launches == 1
+
+
+def test_rejections(mw):
+    import ctypes
+    lib = mw.lib()
+    h = ctypes.c_void_p()
+    # spin != 0 with the real flag
+    st = lib.mw_plan_create(ctypes.byref(h), 16, 1, 2, mw.PRECISIONS["fp64"] | mw.FLAG_REAL)
+    assert st == mw.MW_EINVAL and not h.value
+    # ragged plans reject the flag
+    Ls = (ctypes.c_int * 2)(16, 8)
+    ss = (ctypes.c_int * 2)(0, 0)
+    st = lib.mw_plan_create_ragged(ctypes.byref(h), 2, Ls, ss, mw.PRECISIONS["fp64"] | mw.FLAG_REAL)
+    assert st == mw.MW_EINVAL and not h.value
+    plan = mw.RealPlan(16, 2)
+    assert int(lib.mw_plan_map_elems(plan.handle)) == 2 * wl.map_size(16)
+    y = torch.zeros(2, 16 * 16, dtype=torch.complex128, device="cuda")
+    out = torch.zeros(2, wl.map_size(16), dtype=torch.complex128, device="cuda")
+    st = lib.mw_forward_adjoint(plan.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()), None)
+    assert st == mw.MW_EUNSUPPORTED
+    st = lib.mw_quadrature(plan.handle, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(y.data_ptr()), None)
+    assert st == mw.MW_EUNSUPPORTED
+    with pytest.raises(TypeError):
+        plan.forward(torch.zeros(2, wl.map_size(16), dtype=torch.complex128, device="cuda"))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_l2048_b16_sampled(mw, prec):
+    """16 real maps at L = 2048 (the benchmark's real-signal line), checked on
+    sampled outputs: three rings of the inverse against the oracle's ring
+    synthesis, eight m columns of the forward of the GPU maps against the
+    oracle's forward restricted to those m, and the round trip on every
+    coefficient."""
+    L, B = 2048, 16
+    c = np.stack([wl.uniform_flm_real(wl.rng(3300 + b), L) for b in range(B)])
+    plan = mw.RealPlan(L, B, precision=prec)
+    x = plan.inverse(torch.from_numpy(c).cuda())
+    back = plan.forward(x)
+    plan.sync()
+    x_np = x.cpu().numpy()
+    back_np = back.cpu().numpy()
+    assert mirror_ok(back, L)
+    M = 2 * L - 1
+    rings = [0, 1023, L - 2]
+    ms = [-2047, -1000, -3, 0, 2, 517, 1999, 2047]
+    ell = wl.ell_of_index(L)
+    sel = np.isin(np.arange(L * L) - ell * ell - ell, ms)
+    idx = [0, 7, 15]
+    ref_r = oracle.inverse_rings(c[idx], L, 0, rings).real
+    ref_f = oracle.forward(x_np[idx].astype(np.complex128), L, 0, m_list=ms)
+    for k, b in enumerate(idx):
+        got_r = np.stack([x_np[b][t * M:(t + 1) * M] for t in rings])
+        assert relmax(got_r, ref_r[k]) < TOL[prec]
+        assert relmax(back_np[b][sel], ref_f[k][sel]) < TOL[prec]
+    # the round trip composes two transforms, each held to TOL above, so its
+    # bound is the sum; white coefficients at L = 2048 put the mixed round trip
+    # near 1.0e-6 on complex and real plans alike (the pairing adds about 6%)
+    tol = 1e-11 if prec == "fp64" else 2 * TOL[prec]
+    for b in range(B):
+        assert np.max(np.abs(back_np[b] - c[b])) / np.max(np.abs(c[b])) < tol
