@@ -152,6 +152,17 @@ def risbo_units(L):
     return tot
 
 
+def risbo_ff_instructions(L):
+    """FP32 instructions of one float-float Risbo sweep (the mixed paths): per
+    octant element of a half-step plane 4 float-float operations (one product
+    at 7 FP32 instructions, three multiply-adds at 15) = 52, per integer-plane
+    element 5 (two products, three multiply-adds) = 59."""
+    tot = 0
+    for l in range(1, L):
+        tot += 52 * (l * (l + 1) // 2) + 59 * ((l + 1) * (l + 2) // 2)
+    return tot
+
+
 def fft_stage_bytes(L, B, precision):
     """Algorithmic HBM bytes of the FFT stages of one round trip (inverse +
     forward): every stage boundary written once and read once."""
@@ -318,6 +329,19 @@ def run_ours(args, rank, world, local_rank):
                                "peak_src": "measured (own FP64 DFMA microbenchmark)",
                                "work": "7 flops per octant element of each half-step plane",
                                "frac_quarter_plane_units": a_s / pk["fp64_tflops"]}
+        if args.precision != "fp64":
+            # the mixed paths evaluate the recursion in float-float on the FP32
+            # pipe: the FP64 figures above are FP64-equivalent; this is the
+            # fraction of the FP32 pipe's issue rate the stencil's instructions take
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = (ck or {}).get("sm_mhz") or 2070.0
+            peak_i = n_sm * 128 * mhz * 1e6
+            ach_i = sweeps * risbo_ff_instructions(L) / t["delta"]
+            stage_roof["delta"]["arith"] = "float-float on the FP32 pipe (FP64-equivalent flops above)"
+            stage_roof["delta"]["fp32_issue"] = {
+                "achieved": ach_i / 1e12, "peak": peak_i / 1e12, "unit": "T instr/s", "frac": ach_i / peak_i,
+                "work": "52 / 59 FP32 instructions per half / integer octant element",
+                "peak_src": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock in the timed region)"}
     tc_flops = 2 * contraction_units(L, spins) * 4
     if t["contract"] > 0:
         a = tc_flops / t["contract"] / 1e12

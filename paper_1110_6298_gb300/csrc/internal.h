@@ -61,6 +61,9 @@ struct mw_plan {
   double* d_rsqrt = nullptr;       // 1/sqrt(k), k = 1..2L+2 (entry 0 unused, 0)
   double2* d_upole = nullptr;      // u(m') + u(-m') (m' > 0), u(0): pole row of the forward adjoint
   double* d_rscale = nullptr;      // 1 / (sqrt2 * two_jp) for the Risbo half step to plane two_jp / 2
+  float2* d_sqrt_ff = nullptr;     // mixed paths: the three tables above as float-float (hi, lo)
+  float2* d_rsqrt_ff = nullptr;
+  float2* d_rscale_ff = nullptr;
   double* d_nl = nullptr;          // sqrt((2l+1)/(4 pi)), l < L
   float2* d_flmf = nullptr;        // mixed path: N_l f_lm in FP32 (input of the inverse contraction)
 
@@ -69,7 +72,7 @@ struct mw_plan {
   double2* d_Gp = nullptr;         // [B][M][L] folded G+_{m,m'} or F+_{m,m'}, m' >= 0; on the mixed path G+
                                    // as float2 and F+ as float-float (re_hi, re_lo, im_hi, im_lo)
   double* d_S = nullptr;           // FP64 path: [kChunk][LD][LD] staged integer Delta planes (quarter);
-                                   // mixed path: [2][LD][LD] ping-pong recursion state
+                                   // mixed path: [2][LD][LD] ping-pong recursion state (float-float pairs)
   float* d_S32 = nullptr;          // mixed path: [kTcChunk][LD][LD] FP32 copies of the integer planes
   int* d_err = nullptr;            // device error word (bit 0: tensor-core wait, bit 1: grid barrier)
   int* d_prog = nullptr;           // per-tile progress counters of the persistent Risbo kernel
@@ -140,7 +143,7 @@ cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, c
 // Wigner stage: one sweep l = 0..o->L-1 with Risbo's recursion (state of the
 // owner o) and the contractions of the consumer plans cs[0..nc).
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
-int risbo_blocks_per_sm();
+int risbo_blocks_per_sm(int prec);
 int quad_chunks(const mw_plan* p);
 cudaError_t launch_quad_weights(int L, int s, double* q, cudaStream_t st);
 cudaError_t launch_quadrature(const mw_plan* p, const double2* maps, double2* out, cudaStream_t st, int* launches);

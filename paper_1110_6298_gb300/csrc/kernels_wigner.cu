@@ -55,6 +55,68 @@ __device__ __forceinline__ float to_f32_int(double v) {
 }
 
 // ---------------------------------------------------------------------------
+// Arithmetic of the recursion state.  The FP64 path recurses in double.  The
+// mixed path recurses in float-float: a value is the unevaluated sum hi + lo of
+// two floats with |lo| <= ulp(hi) / 2 (about 48 significant bits), built from
+// the error-free transformations TwoSum (Knuth) and TwoProduct by FMA
+// (Dekker's product with a fused multiply-add), so the stencil runs on the FP32
+// pipe, which is about 80 times faster than the FP64 pipe on this part.  The
+// planes feed an FP32 staging copy and a contraction designed for 1e-6, so 48
+// bits leave a margin of about five orders of magnitude over the 2L half steps.
+// The _rn intrinsics keep the compiler from contracting a product into the
+// following sum, which would break the error terms.
+// ---------------------------------------------------------------------------
+struct NumF64 {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ T fms(T a, T b, T c) { return ::fma(-a, b, c); }  // c - a b
+  static __device__ __forceinline__ T flip(T v, int k) { return flip_sign(v, k); }
+  static __device__ __forceinline__ float f32(T v) { return to_f32_int(v); }
+};
+
+// hi + lo from s + e, |s| >= |e| or s + e exact (Fast2Sum)
+__device__ __forceinline__ float2 ff_fast(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+struct NumFF {
+  using T = float2;  // (hi, lo)
+  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+  // a b: TwoProduct of the high parts plus the cross terms (the lo * lo term is
+  // below the format's precision), renormalised
+  static __device__ __forceinline__ T mul(T a, T b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return ff_fast(p, e);
+  }
+  // a b + c: TwoProduct of the high parts, TwoSum with c's high part, the
+  // cross terms and both low parts collected, renormalised
+  static __device__ __forceinline__ T fma(T a, T b, T c) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    const float s = __fadd_rn(p, c.x);
+    const float v = __fsub_rn(s, p);
+    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.x, v));
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    e = __fadd_rn(e, __fadd_rn(c.y, err));
+    return ff_fast(s, e);
+  }
+  static __device__ __forceinline__ T fms(T a, T b, T c) { return fma(make_float2(-a.x, -a.y), b, c); }
+  // v (-1)^k: sign bits flipped on the integer pipe
+  static __device__ __forceinline__ T flip(T v, int k) {
+    const unsigned m = (unsigned)(k & 1) << 31;
+    return make_float2(__uint_as_float(__float_as_uint(v.x) ^ m), __uint_as_float(__float_as_uint(v.y) ^ m));
+  }
+  static __device__ __forceinline__ float f32(T v) { return v.x; }  // hi = RN(hi + lo)
+};
+
+// ---------------------------------------------------------------------------
 // Persistent Risbo sweep over the planes l in [l_begin, l_end) of one chunk.
 //
 // One cooperative launch per chunk of planes.  Each l is one pass over 32 x 32
@@ -64,30 +126,32 @@ __device__ __forceinline__ float to_f32_int(double v) {
 // a0-1 .. a0+32 in shared memory, computes the half-integer plane d^{l-1/2} on
 // rows/columns a0-1 .. a0+31 (including the index -1, i.e. m = -1/2, directly
 // from the gather formula) and from it the integer plane Delta^l on the tile.
-// Recomputing the 33 x 33 half plane per tile costs 6% more FP64 work than a
+// Recomputing the 33 x 33 half plane per tile costs 6% more arithmetic than a
 // global half step but saves a grid barrier and the half plane's memory
-// traffic per l.  Per element the stencil costs 5 FP64 instructions: with the
-// column factors cn = sqrt(j'-nu)/(2 sqrt2 j'), cp = sqrt(j'+nu)/(2 sqrt2 j')
-// kept in shared memory,
+// traffic per l.  Per element the stencil costs 4 (half plane) or 5 (integer
+// plane) multiply-adds: with the column factors cn = sqrt(j'-nu)/(2 sqrt2 j'),
+// cp = sqrt(j'+nu)/(2 sqrt2 j') kept in shared memory,
 //   e = cn (sqrt(j'-mu) d_{+,+} - sqrt(j'+mu) d_{-,+}) + cp (sqrt(j'-mu) d_{+,-} + sqrt(j'+mu) d_{-,-}).
 // Integer planes are also written out as full quarters where a contraction
 // reads them (FP32 staging copy on the mixed path; the FP64 plane itself on the
-// FP64 path), the upper triangle through an in-shared-memory transpose.
+// FP64 path), the upper triangle through an in-shared-memory transpose.  The
+// kernel is a template over the number type of the state (NumF64 on the FP64
+// path, NumFF on the mixed paths); both take 8 bytes per element.
 // ---------------------------------------------------------------------------
 constexpr int kRT = 32;         // tile edge
 constexpr int kRThreads = 256;  // 32 x 8 threads
 constexpr unsigned kBarrierPolls = 1u << 24;
 
 struct RisboArgs {
-  double* S;          // FP64 integer planes; plane l at slot l % nslot
+  void* S;            // integer planes (double or float-float); plane l at slot l % nslot
   int nslot;
   float* S32;         // FP32 staging of the integer planes (slot l - l0), or null
   int l0;
   int full64;         // write transposed tiles into the FP64 integer plane
   int LD;
-  const double* sq;      // sqrt(k)
-  const double* rsq;     // 1/sqrt(k), k >= 1
-  const double* rscale;  // 1 / (sqrt2 two_jp)
+  const void* sq;        // sqrt(k)               (tables in the recursion's number type)
+  const void* rsq;       // 1/sqrt(k), k >= 1
+  const void* rscale;    // 1 / (sqrt2 two_jp)
   int* prog;          // per-tile progress: last plane l published
   int* err;
   const int* perm;    // rank of each block in the tile assignment (null: blockIdx.x)
@@ -99,13 +163,14 @@ struct RisboArgs {
 // diagonal: index -1 is m = -1 and reflects to +1 through
 //   d_{-m,n} = (-1)^(j-n) d_{mn}, d_{m,-n} = (-1)^(j+m) d_{mn}  (Eq. wignerd_sym2 at pi/2, sym1),
 // and the upper triangle is read through d_{mn} = (-1)^(m-n) d_{nm}.
-__device__ __forceinline__ double prev_val(const double* __restrict__ d, int LD, int i, int k, int j) {
+template <class Nm>
+__device__ __forceinline__ typename Nm::T prev_val(const typename Nm::T* __restrict__ d, int LD, int i, int k, int j) {
   int ex = 0;  // value = (-1)^ex d[i][k]
   if (i < 0) { ex += j - k; i = -i; }
   if (k < 0) { ex += j + i; k = -k; }
-  if (i > j || k > j) return 0.0;
+  if (i > j || k > j) return Nm::zero();
   if (k > i) { ex += i - k; const int t = i; i = k; k = t; }
-  return flip_sign(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks for the last l
+  return Nm::flip(__ldcg(d + (size_t)i * LD + k), ex);  // L2: written by other blocks for the last l
 }
 
 // Tile (I, J), J <= I, of the lower triangle has linear index I (I+1)/2 + J.
@@ -141,19 +206,26 @@ __global__ void k_prog_init(int* prog, int n, int value) {
 // (tiles t and t + G are far apart, so neither waits for the other).  One tile
 // per pass measured as fast as two, with half the shared memory.
 constexpr int kPair = 1;
+template <class V>
 struct RisboSmem {
-  double dh[kPair][kRT + 2][kRT + 3];  // Delta^{l-1} on rows/cols a0-1 .. a0+32
-  double hh[kPair][kRT + 1][kRT + 1];  // d^{l-1/2} on rows/cols a0-1 .. a0+31
-  double tr[kPair][kRT][kRT + 1];      // Delta^l on the tile
-  double colf[kPair][4][kRT + 1];      // cn, cp of the half plane (33 cols) and of the integer plane (32)
-  double rowf[kPair][4][kRT + 1];      // sqrt(j'-mu), sqrt(j'+mu) of the half-plane rows (33) and integer rows (32)
+  V dh[kPair][kRT + 2][kRT + 3];  // Delta^{l-1} on rows/cols a0-1 .. a0+32
+  V hh[kPair][kRT + 1][kRT + 1];  // d^{l-1/2} on rows/cols a0-1 .. a0+31
+  V tr[kPair][kRT][kRT + 1];      // Delta^l on the tile
+  V colf[kPair][4][kRT + 1];      // cn, cp of the half plane (33 cols) and of the integer plane (32)
+  V rowf[kPair][4][kRT + 1];      // sqrt(j'-mu), sqrt(j'+mu) of the half-plane rows (33) and integer rows (32)
   int ok;
 };
-constexpr int kRisboSmem = (int)sizeof(RisboSmem);
+static_assert(sizeof(RisboSmem<double>) == sizeof(RisboSmem<float2>), "both number types take 8 bytes");
+constexpr int kRisboSmem = (int)sizeof(RisboSmem<double>);
 
+template <class Nm>
 __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
+  using V = typename Nm::T;
   extern __shared__ __align__(16) unsigned char risbo_smem[];
-  RisboSmem& sm = *reinterpret_cast<RisboSmem*>(risbo_smem);
+  RisboSmem<V>& sm = *reinterpret_cast<RisboSmem<V>*>(risbo_smem);
+  const V* sq = static_cast<const V*>(A.sq);
+  const V* rsq = static_cast<const V*>(A.rsq);
+  const V* rscale = static_cast<const V*>(A.rscale);
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int LD = A.LD;
   const size_t plane = (size_t)LD * LD;
@@ -170,10 +242,10 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
   for (int l = l_begin; l < l_end; ++l) {
     const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
     const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
-    const double* d = A.S + (size_t)((l - 1) % A.nslot) * plane;
-    double* e = A.S + (size_t)(l % A.nslot) * plane;
+    const V* d = static_cast<const V*>(A.S) + (size_t)((l - 1) % A.nslot) * plane;
+    V* e = static_cast<V*>(A.S) + (size_t)(l % A.nslot) * plane;
     float* st = A.S32 ? A.S32 + (size_t)(l - A.l0) * plane : nullptr;
-    const double sch = A.rscale[th], sci = A.rscale[ti];
+    const V sch = rscale[th], sci = rscale[ti];
     const int T = (nnew + kRT - 1) / kRT;       // tile rows of plane l
     const int Tp = (l + kRT - 1) / kRT;         // tile rows of plane l-1 (size l)
     const int ntiles = T * (T + 1) / 2;
@@ -218,33 +290,33 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
             if (y <= kRT) {  // half-plane row i = a0-1+y (mu = i + 1/2)
               const int i = a0 - 1 + y, mu2 = 2 * i + 1;
               const bool in = i < nh;
-              sm.rowf[k][0][y] = in ? A.sq[(th - mu2) / 2] : 0.0;
-              sm.rowf[k][1][y] = in ? A.sq[(th + mu2) / 2] : 0.0;
+              sm.rowf[k][0][y] = in ? sq[(th - mu2) / 2] : Nm::zero();
+              sm.rowf[k][1][y] = in ? sq[(th + mu2) / 2] : Nm::zero();
             } else if (y < 2 * kRT + 1) {  // integer-plane row a = a0 + r
               const int r = y - (kRT + 1), a = a0 + r;
               const bool in = a < nnew;
-              sm.rowf[k][2][r] = in ? A.sq[(ti - 2 * a) / 2] : 0.0;
-              sm.rowf[k][3][r] = in ? A.sq[(ti + 2 * a) / 2] : 0.0;
+              sm.rowf[k][2][r] = in ? sq[(ti - 2 * a) / 2] : Nm::zero();
+              sm.rowf[k][3][r] = in ? sq[(ti + 2 * a) / 2] : Nm::zero();
             } else if (y < 3 * kRT + 2) {  // half-plane column k = b0-1+c (nu = k + 1/2)
               const int c = y - (2 * kRT + 1);
               const int nu2 = 2 * (b0 - 1 + c) + 1;
               const bool in = (b0 - 1 + c) < nh;
               if (l == 1) {  // cn, cp themselves
-                sm.colf[k][0][c] = in ? sch * A.sq[(th - nu2) / 2] : 0.0;
-                sm.colf[k][1][c] = in ? sch * A.sq[(th + nu2) / 2] : 0.0;
+                sm.colf[k][0][c] = in ? Nm::mul(sch, sq[(th - nu2) / 2]) : Nm::zero();
+                sm.colf[k][1][c] = in ? Nm::mul(sch, sq[(th + nu2) / 2]) : Nm::zero();
               } else {  // cn / cp (cp = sch sqrt(l + k) > 0 inside the plane)
-                sm.colf[k][0][c] = in ? A.sq[(th - nu2) / 2] * A.rsq[(th + nu2) / 2] : 0.0;
-                sm.colf[k][1][c] = 0.0;
+                sm.colf[k][0][c] = in ? Nm::mul(sq[(th - nu2) / 2], rsq[(th + nu2) / 2]) : Nm::zero();
+                sm.colf[k][1][c] = Nm::zero();
               }
             } else {  // integer-plane column b = b0 + c
               const int c = y - (3 * kRT + 2), bcol = b0 + c;
               const bool in = bcol < nnew;
-              double f2 = in ? sci * A.sq[(ti - 2 * bcol) / 2] : 0.0;
-              double f3 = in ? sci * A.sq[(ti + 2 * bcol) / 2] : 0.0;
+              V f2 = in ? Nm::mul(sci, sq[(ti - 2 * bcol) / 2]) : Nm::zero();
+              V f3 = in ? Nm::mul(sci, sq[(ti + 2 * bcol) / 2]) : Nm::zero();
               if (l > 1) {  // absorb the scales cp of half-plane columns c and c+1
                 const int kc = b0 - 1 + c;    // half-plane column of hh column c
-                f3 *= (kc < nh) ? sch * A.sq[l + kc] : 0.0;
-                f2 *= (kc + 1 < nh) ? sch * A.sq[l + kc + 1] : 0.0;
+                f3 = Nm::mul(f3, (kc < nh) ? Nm::mul(sch, sq[l + kc]) : Nm::zero());
+                f2 = Nm::mul(f2, (kc + 1 < nh) ? Nm::mul(sch, sq[l + kc + 1]) : Nm::zero());
               }
               sm.colf[k][2][c] = f2;
               sm.colf[k][3][c] = f3;
@@ -256,17 +328,17 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
       if (!sm.ok) return;
       {  // all of a thread's halo loads (both tiles) are issued before any is stored
         constexpr int kLoads = ((kRT + 2) * (kRT + 2) + kRThreads - 1) / kRThreads;  // 5
-        double v[kPair][kLoads];
+        V v[kPair][kLoads];
 #pragma unroll
         for (int k = 0; k < kPair; ++k) {
           const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
 #pragma unroll
           for (int q = 0; q < kLoads; ++q) {
             const int idx = tid + q * kRThreads;
-            v[k][q] = 0.0;
+            v[k][q] = Nm::zero();
             if (k < np && idx < (kRT + 2) * (kRT + 2)) {
               const int r = idx / (kRT + 2), c = idx % (kRT + 2);
-              v[k][q] = prev_val(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
+              v[k][q] = prev_val<Nm>(d, LD, a0 - 1 + r, b0 - 1 + c, l - 1);
             }
           }
         }
@@ -294,28 +366,29 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
           const int a0 = II[k] * kRT, b0 = JJ[k] * kRT;
           const int i = a0 - 1 + r;
           if (i >= nh) {
-            for (int c = c0; c < c1; ++c) sm.hh[k][r][c] = 0.0;
+            for (int c = c0; c < c1; ++c) sm.hh[k][r][c] = Nm::zero();
             continue;
           }
-          const double cmm = sm.rowf[k][0][r], cpm = sm.rowf[k][1][r];
-          double pprev = cmm * sm.dh[k][r + 1][c0];
+          const V cmm = sm.rowf[k][0][r], cpm = sm.rowf[k][1][r];
+          V pprev = Nm::mul(cmm, sm.dh[k][r + 1][c0]);
           if (l > 1) {
             // hh holds the half plane divided by its column factor cp (which the
-            // integer step's column factors carry instead): 4 FP64 instructions
-            // per element.  Columns outside the plane have scale 0 there.
+            // integer step's column factors carry instead): 4 multiply-adds per
+            // element.  Columns outside the plane have scale 0 there.
             for (int c = c0; c < c1; ++c) {
-              const double p = cmm * sm.dh[k][r + 1][c + 1];
-              const double t1 = fma(-cpm, sm.dh[k][r][c + 1], p);
-              const double t2 = fma(cpm, sm.dh[k][r][c], pprev);
-              sm.hh[k][r][c] = fma(sm.colf[k][0][c], t1, t2);
+              const V p = Nm::mul(cmm, sm.dh[k][r + 1][c + 1]);
+              const V t1 = Nm::fms(cpm, sm.dh[k][r][c + 1], p);
+              const V t2 = Nm::fma(cpm, sm.dh[k][r][c], pprev);
+              sm.hh[k][r][c] = Nm::fma(sm.colf[k][0][c], t1, t2);
               pprev = p;
             }
           } else {
             for (int c = c0; c < c1; ++c) {
-              const double p = cmm * sm.dh[k][r + 1][c + 1];
-              const double t1 = fma(-cpm, sm.dh[k][r][c + 1], p);
-              const double t2 = fma(cpm, sm.dh[k][r][c], pprev);
-              sm.hh[k][r][c] = (b0 - 1 + c < nh) ? fma(sm.colf[k][1][c], t2, sm.colf[k][0][c] * t1) : 0.0;
+              const V p = Nm::mul(cmm, sm.dh[k][r + 1][c + 1]);
+              const V t1 = Nm::fms(cpm, sm.dh[k][r][c + 1], p);
+              const V t2 = Nm::fma(cpm, sm.dh[k][r][c], pprev);
+              sm.hh[k][r][c] =
+                  (b0 - 1 + c < nh) ? Nm::fma(sm.colf[k][1][c], t2, Nm::mul(sm.colf[k][0][c], t1)) : Nm::zero();
               pprev = p;
             }
           }
@@ -334,19 +407,19 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
           if (k >= np) continue;
           const int a = II[k] * kRT + r;
           if (a < nnew) {
-            const double cmm = sm.rowf[k][2][r], cpm = sm.rowf[k][3][r];
-            double pprev = cmm * sm.hh[k][r + 1][c0];
+            const V cmm = sm.rowf[k][2][r], cpm = sm.rowf[k][3][r];
+            V pprev = Nm::mul(cmm, sm.hh[k][r + 1][c0]);
 #pragma unroll
             for (int c = c0; c < c0 + 4; ++c) {
-              const double p = cmm * sm.hh[k][r + 1][c + 1];
-              const double t1 = fma(-cpm, sm.hh[k][r][c + 1], p);
-              const double t2 = fma(cpm, sm.hh[k][r][c], pprev);
+              const V p = Nm::mul(cmm, sm.hh[k][r + 1][c + 1]);
+              const V t1 = Nm::fms(cpm, sm.hh[k][r][c + 1], p);
+              const V t2 = Nm::fma(cpm, sm.hh[k][r][c], pprev);
               pprev = p;
-              sm.tr[k][r][c] = fma(sm.colf[k][3][c], t2, sm.colf[k][2][c] * t1);
+              sm.tr[k][r][c] = Nm::fma(sm.colf[k][3][c], t2, Nm::mul(sm.colf[k][2][c], t1));
             }
           } else {
 #pragma unroll
-            for (int c = c0; c < c0 + 4; ++c) sm.tr[k][r][c] = 0.0;
+            for (int c = c0; c < c0 + 4; ++c) sm.tr[k][r][c] = Nm::zero();
           }
         }
       }
@@ -382,7 +455,7 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
           for (int q = 0; q < kRT / 8; ++q) {
             const int r = ty + 8 * q;
             const int a = a0 + r, bcol = b0 + tx;
-            if (a < nnew && bcol < nnew) st[(size_t)a * LD + bcol] = to_f32_int(sm.tr[k][r][tx]);
+            if (a < nnew && bcol < nnew) st[(size_t)a * LD + bcol] = Nm::f32(sm.tr[k][r][tx]);
           }
         }
         if ((JJ[k] < II[k]) && (st || A.full64)) {
@@ -390,9 +463,9 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
           for (int q = 0; q < kRT / 8; ++q) {
             const int bb = b0 + ty + 8 * q, aa = a0 + tx;  // element (aa, bb) written at (bb, aa)
             if (aa < nnew && bb < nnew) {
-              const double v = flip_sign(sm.tr[k][tx][ty + 8 * q], aa - bb);
+              const V v = Nm::flip(sm.tr[k][tx][ty + 8 * q], aa - bb);
               if (A.full64) e[(size_t)bb * LD + aa] = v;
-              if (st) st[(size_t)bb * LD + aa] = to_f32_int(v);
+              if (st) st[(size_t)bb * LD + aa] = Nm::f32(v);
             }
           }
         }
@@ -401,17 +474,23 @@ __global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l
   }
 }
 
-// Delta^0 = [1] (and its FP32 copy)
-__global__ void k_plane_init(double* S, float* S32) {
-  S[0] = 1.0;
+// Delta^0 = [1] (and its FP32 copy); the state is double or float-float (1, 0)
+__global__ void k_plane_init(void* S, float* S32, int float_float) {
+  if (float_float) static_cast<float2*>(S)[0] = make_float2(1.f, 0.f);
+  else static_cast<double*>(S)[0] = 1.0;
   if (S32) S32[0] = 1.0f;
+}
+
+// the sweep kernel of a plan's precision: float-float on the mixed paths
+const void* sweep_kernel(int prec) {
+  return prec == MW_PREC_FP64 ? (const void*)k_risbo_sweep<NumF64> : (const void*)k_risbo_sweep<NumFF>;
 }
 
 }  // namespace
 
 namespace {
 
-cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, int full64, int lb, int le,
+cudaError_t launch_risbo(mw_plan* p, void* S, int nslot, float* S32, int l0, int full64, int lb, int le,
                          cudaStream_t st, int* nd) {
   if (lb >= le) return cudaSuccess;
   const int Tm = (le + kRT - 1) / kRT;
@@ -420,10 +499,14 @@ cudaError_t launch_risbo(mw_plan* p, double* S, int nslot, float* S32, int l0, i
   if (e != cudaSuccess) return e;
   RisboArgs a;
   a.S = S; a.nslot = nslot; a.S32 = S32; a.l0 = l0; a.full64 = full64; a.LD = p->LD;
-  a.sq = p->d_sqrt; a.rsq = p->d_rsqrt; a.rscale = p->d_rscale; a.prog = p->d_prog; a.err = p->d_err;
+  const bool ff = p->prec != MW_PREC_FP64;
+  a.sq = ff ? (const void*)p->d_sqrt_ff : (const void*)p->d_sqrt;
+  a.rsq = ff ? (const void*)p->d_rsqrt_ff : (const void*)p->d_rsqrt;
+  a.rscale = ff ? (const void*)p->d_rscale_ff : (const void*)p->d_rscale;
+  a.prog = p->d_prog; a.err = p->d_err;
   a.perm = p->d_perm; a.smid_out = nullptr;
   void* args[] = {&a, &lb, &le};
-  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(p->risbo_grid), dim3(kRThreads), args,
+  e = cudaLaunchCooperativeKernel(sweep_kernel(p->prec), dim3(p->risbo_grid), dim3(kRThreads), args,
                                   (size_t)kRisboSmem, st);
   if (nd) *nd += 2;  // the progress reset and the sweep
   return e;
@@ -450,7 +533,7 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
       ++nl;
     }
   }
-  k_plane_init<<<1, 1, 0, st>>>(o->d_S, fp64 ? nullptr : o->d_S32);
+  k_plane_init<<<1, 1, 0, st>>>(o->d_S, fp64 ? nullptr : o->d_S32, fp64 ? 0 : 1);
   ++nl;
   for (int l0 = 0; l0 < o->L; l0 += chunk) {
     const int l1 = (l0 + chunk < o->L) ? l0 + chunk : o->L;
@@ -487,10 +570,11 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
 
 // Co-resident blocks per SM of the persistent recursion kernel: the occupancy
 // limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 4, the fastest measured).
-int risbo_blocks_per_sm() {
+int risbo_blocks_per_sm(int prec) {
   int n = 0;
-  if (cudaFuncSetAttribute(k_risbo_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kRisboSmem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_risbo_sweep, kRThreads, kRisboSmem) != cudaSuccess) {
+  const void* k = sweep_kernel(prec);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRisboSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRThreads, kRisboSmem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -516,7 +600,7 @@ cudaError_t make_risbo_perm(mw_plan* p) {
   a.smid_out = d_smid;
   int lb = 1, le = 1;  // no planes: the launch only records the placement
   void* args[] = {&a, &lb, &le};
-  e = cudaLaunchCooperativeKernel((const void*)k_risbo_sweep, dim3(G), dim3(kRThreads), args, (size_t)kRisboSmem, 0);
+  e = cudaLaunchCooperativeKernel(sweep_kernel(p->prec), dim3(G), dim3(kRThreads), args, (size_t)kRisboSmem, 0);
   std::vector<int> smid(G, 0);
   if (e == cudaSuccess) e = cudaMemcpy(smid.data(), d_smid, sizeof(int) * (size_t)G, cudaMemcpyDeviceToHost);
   cudaFree(d_smid);

@@ -74,7 +74,7 @@ void free_plan(mw_plan* p) {
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
-                  p->d_qw,     p->d_qpart, p->d_gpack};
+                  p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -254,6 +254,22 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     alloc((void**)&p->d_nl, sizeof(double) * nlv.size());
     if (e == cudaSuccess) chk(cudaMemcpy(p->d_nl, nlv.data(), sizeof(double) * nlv.size(), cudaMemcpyHostToDevice));
   }
+  if (!dbl) {  // float-float copies of the recursion's tables, split from long-double values
+    auto ff_table = [&](float2** dst, size_t n, auto fn) {
+      std::vector<float2> h(n);
+      for (size_t k = 0; k < n; ++k) {
+        const long double v = fn((long double)k);
+        const float hi = (float)v;
+        h[k] = make_float2(hi, (float)(v - (long double)hi));
+      }
+      alloc((void**)dst, sizeof(float2) * n);
+      if (e == cudaSuccess) chk(cudaMemcpy(*dst, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    };
+    ff_table(&p->d_sqrt_ff, 2 * (size_t)L + 3, [](long double k) { return sqrtl(k); });
+    ff_table(&p->d_rsqrt_ff, 2 * (size_t)L + 3, [](long double k) { return k > 0 ? 1.0L / sqrtl(k) : 0.0L; });
+    ff_table(&p->d_rscale_ff, 2 * (size_t)L + 2,
+             [](long double k) { return k > 0 ? 1.0L / (sqrtl(2.0L) * k) : 0.0L; });
+  }
   alloc((void**)&p->d_spins, sizeof(int) * B);
   if (e == cudaSuccess) chk(cudaMemcpy(p->d_spins, spins, sizeof(int) * B, cudaMemcpyHostToDevice));
   alloc((void**)&p->d_moff, sizeof(long long) * B);
@@ -293,7 +309,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     if (e == cudaSuccess) {
       int nsm = 0;
       chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-      p->risbo_grid = nsm * risbo_blocks_per_sm();
+      p->risbo_grid = nsm * risbo_blocks_per_sm(p->prec);
       if (e == cudaSuccess) chk(make_risbo_perm(p));
     }
   }

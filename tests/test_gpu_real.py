@@ -95,7 +95,9 @@ def test_round_trip(mw, prec):
     plan = mw.RealPlan(L, B, precision=prec)
     back = plan.forward(plan.inverse(torch.from_numpy(c).cuda()))
     plan.sync()
-    assert relmax(back.cpu().numpy(), c) < (1e-12 if prec == "fp64" else 1e-6)
+    # two transforms, each held to TOL: the round trip's bound is their sum
+    # (white coefficients put the mixed round trip near 1e-6 at any L)
+    assert relmax(back.cpu().numpy(), c) < (1e-12 if prec == "fp64" else 2 * TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
