@@ -185,10 +185,15 @@ def test_full_size_l2048_b16_sampled(mw, prec):
     idx = [0, 7, 15]
     ref_r = oracle.inverse_rings(c[idx], L, 0, rings).real
     ref_f = oracle.forward(x_np[idx].astype(np.complex128), L, 0, m_list=ms)
+    # the oracle is FP64 too and, on white coefficients at L = 2048, carries
+    # rounding errors of the same order as the FP64 path (both round trips
+    # measure 1.13e-12), so the difference of the two is held to the sum of
+    # their bounds
+    tol_o = TOL[prec] + TOL["fp64"]
     for k, b in enumerate(idx):
         got_r = np.stack([x_np[b][t * M:(t + 1) * M] for t in rings])
-        assert relmax(got_r, ref_r[k]) < TOL[prec]
-        assert relmax(back_np[b][sel], ref_f[k][sel]) < TOL[prec]
+        assert relmax(got_r, ref_r[k]) < tol_o
+        assert relmax(back_np[b][sel], ref_f[k][sel]) < tol_o
     # the round trip composes two transforms, each held to TOL above, so its
     # bound is the sum; white coefficients at L = 2048 put the mixed round trip
     # near 1.0e-6 on complex and real plans alike (the pairing adds about 6%)
