@@ -219,7 +219,7 @@ static_assert(sizeof(RisboSmem<double>) == sizeof(RisboSmem<float2>), "both numb
 constexpr int kRisboSmem = (int)sizeof(RisboSmem<double>);
 
 template <class Nm>
-__global__ void __launch_bounds__(kRThreads, 4) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
+__global__ void __launch_bounds__(kRThreads, 5) k_risbo_sweep(RisboArgs A, int l_begin, int l_end) {
   using V = typename Nm::T;
   extern __shared__ __align__(16) unsigned char risbo_smem[];
   RisboSmem<V>& sm = *reinterpret_cast<RisboSmem<V>*>(risbo_smem);
@@ -569,7 +569,9 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
 }  // namespace
 
 // Co-resident blocks per SM of the persistent recursion kernel: the occupancy
-// limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 4, the fastest measured).
+// limit, capped by MW_RISBO_BLOCKS_PER_SM (a tuning knob; default 5: with the
+// float-float state the sweep is latency-bound, and 5 blocks of 48 registers
+// measured 46.1 against 47.6 ms per round trip for 4 blocks of 64).
 int risbo_blocks_per_sm(int prec) {
   int n = 0;
   const void* k = sweep_kernel(prec);
@@ -578,7 +580,7 @@ int risbo_blocks_per_sm(int prec) {
     cudaGetLastError();
     return 1;
   }
-  int cap = 4;
+  int cap = 5;
   if (const char* env = getenv("MW_RISBO_BLOCKS_PER_SM")) {
     const int v = atoi(env);
     if (v >= 1 && v <= 32) cap = v;
