@@ -106,6 +106,58 @@ def delta_plane(l):
     return wigner_plane(2 * l, np.pi / 2)
 
 
+def delta_top_row(l):
+    """Delta^l_{l,m}, m = 0..l, as (mantissa, exponent) pairs with value
+    mantissa * 2^exponent: Delta^l_{l,m} = (-1)^(l-m) 2^-l sqrt(C(2l, l+m)),
+    the closed form of d^l_{l,m}(beta) = sqrt(C(2l, l+m)) cos^(l+m)(beta/2)
+    (-sin(beta/2))^(l-m) at beta = pi/2 (Sec. III-C conventions).  The
+    binomial is an exact integer; the exponent keeps values far below the
+    double range (2^-l at m = l) exact in range."""
+    from math import comb, frexp, sqrt
+    mant = np.empty(l + 1)
+    expo = np.empty(l + 1, dtype=np.int64)
+    for m in range(l + 1):
+        c = comb(2 * l, l + m)
+        e2 = c.bit_length() - 60
+        e2 -= e2 % 2                          # even shift, so the root is exact in the exponent
+        r = sqrt(c >> e2 if e2 > 0 else c << -e2)
+        fm, fe = frexp(r)
+        mant[m] = fm if (l - m) % 2 == 0 else -fm
+        expo[m] = fe + e2 // 2 - l
+    return mant, expo
+
+
+def delta_plane_tn(l):
+    """Quarter plane Delta^l_{m',m}, m', m = 0..l (rows m', columns m), by
+    the Trapani-Navaza recursion (cited in Sec. V-B as the alternative to
+    Risbo's): each column m starts from the top row Delta^l_{l,m} and recurses
+    down the first index with the three-term relation of d^l at beta = pi/2,
+      sqrt((l+m')(l-m'+1)) Delta_{m'-1,m}
+        = 2 m Delta_{m',m} - sqrt((l-m')(l+m'+1)) Delta_{m'+1,m},
+    stopping at m' = 0 (below it the recursion would run into the decaying
+    region near m' = -l, where it is unstable).  Each column is carried as
+    value = x * 2^E with one exponent E per column (rescaled whenever |x|
+    exceeds 2^64), so start values far below the double range stay exact."""
+    mant, expo = delta_top_row(l)
+    m = np.arange(l + 1, dtype=np.float64)
+    E = expo.copy()
+    cur = mant.copy()
+    prev = np.zeros(l + 1)
+    out = np.zeros((l + 1, l + 1))
+    out[l] = np.ldexp(cur, E)
+    for mp in range(l, 0, -1):
+        a = np.sqrt(float((l - mp) * (l + mp + 1)))
+        b = np.sqrt(float((l + mp) * (l - mp + 1)))
+        new = (2.0 * m * cur - a * prev) / b
+        prev, cur = cur, new
+        big = np.abs(cur) > 2.0 ** 64
+        cur = np.where(big, cur * 2.0 ** -64, cur)
+        prev = np.where(big, prev * 2.0 ** -64, prev)
+        E = np.where(big, E + 64, E)
+        out[mp - 1] = np.ldexp(cur, E)
+    return out
+
+
 # --------------------------------------------------------------------------
 # Forward transform (Sec. IV-D), one step per function
 # --------------------------------------------------------------------------
