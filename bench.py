@@ -163,6 +163,67 @@ def risbo_ff_instructions(L):
     return tot
 
 
+def tn_units(L):
+    """Quarter-plane elements of one Trapani-Navaza pass over the planes
+    l < L: every column m of plane l recurses over m' = l .. 0."""
+    return sum((l + 1) ** 2 for l in range(L))
+
+
+def contraction_bytes(L, B, precision):
+    """Algorithmic HBM bytes of both contractions of one round trip: each
+    staged plane read once per direction (FP32 quarter planes on the mixed
+    paths, FP64 on the FP64 path), the forward's G+ read and f_lm written, the
+    inverse's N_l f_lm read and F+ written."""
+    M = 2 * L - 1
+    plane_b = 4 if precision != "fp64" else 8
+    planes = plane_b * tn_units(L)
+    gp = B * M * L * (8 if precision != "fp64" else 16)
+    flm_in = B * L * L * (8 if precision != "fp64" else 16)
+    fplus = B * M * L * 16
+    flm_out = B * L * L * 16
+    return 2 * planes + gp + flm_out + flm_in + fplus
+
+
+def delta_roofline(recursion, L, seconds, pk, fp32_issue, n_sm, mhz):
+    """Roofline entry of the Wigner-plane stage (two recursions per round trip)
+    for the recursion that ran: "risbo_f64" (double state, FP64 pipe),
+    "risbo_ff" (float-float state, FP32 pipe) or "tn" (Trapani-Navaza,
+    float-float, FP32 pipe and FP32 staging writes)."""
+    sweeps = 2
+    issue_src = f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock in the timed region)"
+    if recursion == "tn":
+        units = sweeps * tn_units(L)
+        instr = 29 * units          # float-float: two products (7 each) and one multiply-add (15)
+        nbytes = 4 * units          # every quarter-plane element staged once in FP32
+        t_i, t_b = instr / fp32_issue, nbytes / (pk["hbm_gbs"] * 1e9)
+        issue = {"achieved": instr / seconds / 1e12, "peak": fp32_issue / 1e12, "unit": "T instr/s",
+                 "frac": t_i / seconds, "work": "29 FP32 instructions per quarter-plane element",
+                 "peak_src": issue_src}
+        hbm = {"achieved": nbytes / seconds / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": t_b / seconds,
+               "work": "4 bytes (FP32 staging) per quarter-plane element", "peak_src": pk["src"]}
+        out = dict(issue, bound="alu") if t_i >= t_b else dict(hbm, bound="hbm")
+        out.update(kernel="k_tn_planes", recursion="Trapani-Navaza", fp32_issue=issue, hbm=hbm,
+                   floor_ms=1e3 * max(t_i, t_b))
+        return out
+    fl = sweeps * risbo_units(L) * 7
+    a = fl / seconds / 1e12
+    out = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+           "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep", "recursion": "Risbo",
+           "peak_src": "measured (own FP64 DFMA microbenchmark)",
+           "work": "7 flops per octant element of each half-step plane",
+           "frac_quarter_plane_units": sweeps * 7.0 * L ** 3 / seconds / 1e12 / pk["fp64_tflops"],
+           "floor_ms": 1e3 * fl / (pk["fp64_tflops"] * 1e12)}
+    if recursion == "risbo_ff":
+        instr = sweeps * risbo_ff_instructions(L)
+        out["arith"] = "float-float on the FP32 pipe (FP64-equivalent flops above)"
+        out["fp32_issue"] = {"achieved": instr / seconds / 1e12, "peak": fp32_issue / 1e12, "unit": "T instr/s",
+                             "frac": instr / fp32_issue / seconds,
+                             "work": "52 / 59 FP32 instructions per half / integer octant element",
+                             "peak_src": issue_src}
+        out["floor_ms"] = 1e3 * instr / fp32_issue
+    return out
+
+
 def fft_stage_bytes(L, B, precision):
     """Algorithmic HBM bytes of the FFT stages of one round trip (inverse +
     forward): every stage boundary written once and read once."""
@@ -291,6 +352,34 @@ def run_ours(args, rank, world, local_rank):
     rplan.close()
     del rplan, cr, rmap, rout
 
+    # the same round trip with Risbo's recursion for the Wigner planes (the
+    # mixed plans' default is the Trapani-Navaza recursion)
+    rb_line = None
+    if args.precision != "fp64":
+        rb = mw.Plan(L, spins, precision=args.precision, graph=True, delta="risbo")
+        rb_out = torch.empty_like(flm)
+
+        def risbo_roundtrip():
+            rb.inverse(flm, out=maps)
+            rb.forward(maps, out=rb_out)
+
+        for _ in range(2):
+            risbo_roundtrip()
+        rb.sync()
+        rb_err = float((rb_out - flm).abs().max().item() / flm.abs().max().item())
+        rb_ms, _ = timed(risbo_roundtrip, K)
+        rb.set_timing(True)
+        rb.stage_times(reset=True)
+        rb.inverse(flm, out=maps)
+        rb.forward(maps, out=rb_out)
+        torch.cuda.synchronize(dev)
+        rb_stages = {k: v[0] for k, v in rb.stage_times(reset=True).items()}
+        rb.close()
+        del rb, rb_out
+        rb_line = {"value": whole_job_value(world, B, K, rb_ms / 1e3), "unit": "transforms/s",
+                   "ms_per_step": rb_ms / K, "rel_err": rb_err, "stage_ms_per_step": rb_stages,
+                   "what": "the same round trip with Risbo's recursion (MW_FLAG_DELTA_RISBO)"}
+
     # end to end: the round trip through the C ABI with pinned host buffers,
     # host<->device copies inside the timed region
     flm_pin = flm_h.pin_memory()
@@ -318,68 +407,57 @@ def run_ours(args, rank, world, local_rank):
     pk_hbm = pk["hbm_gbs"]
     fb = fft_stage_bytes(L, B, args.precision)
     t = {k: v / 1e3 for k, v in stages.items()}  # seconds per round trip
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (ck or {}).get("sm_mhz") or 2070.0
+    fp32_issue = n_sm * 128 * mhz * 1e6  # FP32 instructions per second
+    recursion = "risbo_f64" if args.precision == "fp64" else "tn"
     stage_roof = {}
-    sweeps = 2  # one recursion per direction
     if t["delta"] > 0:
-        fl = sweeps * risbo_units(L) * 7
-        a = fl / t["delta"] / 1e12
-        a_s = sweeps * 7.0 * L ** 3 / t["delta"] / 1e12
-        stage_roof["delta"] = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                               "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep",
-                               "peak_src": "measured (own FP64 DFMA microbenchmark)",
-                               "work": "7 flops per octant element of each half-step plane",
-                               "frac_quarter_plane_units": a_s / pk["fp64_tflops"]}
-        if args.precision != "fp64":
-            # the mixed paths evaluate the recursion in float-float on the FP32
-            # pipe: the FP64 figures above are FP64-equivalent; this is the
-            # fraction of the FP32 pipe's issue rate the stencil's instructions take
-            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-            mhz = (ck or {}).get("sm_mhz") or 2070.0
-            peak_i = n_sm * 128 * mhz * 1e6
-            ach_i = sweeps * risbo_ff_instructions(L) / t["delta"]
-            stage_roof["delta"]["arith"] = "float-float on the FP32 pipe (FP64-equivalent flops above)"
-            stage_roof["delta"]["fp32_issue"] = {
-                "achieved": ach_i / 1e12, "peak": peak_i / 1e12, "unit": "T instr/s", "frac": ach_i / peak_i,
-                "work": "52 / 59 FP32 instructions per half / integer octant element",
-                "peak_src": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock in the timed region)"}
+        stage_roof["delta"] = delta_roofline(recursion, L, t["delta"], pk, fp32_issue, n_sm, mhz)
     tc_flops = 2 * contraction_units(L, spins) * 4
+    c_bytes = contraction_bytes(L, B, args.precision)
+    tc_peak = {"mixed": pk["bf16_tflops"], "mixed_tf32": pk["bf16_tflops"] * 0.5}.get(args.precision, 1.045)
     if t["contract"] > 0:
-        a = tc_flops / t["contract"] / 1e12
-        if args.precision == "mixed":
-            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                                      "frac": a / pk["bf16_tflops"], "kernel": "k_tc_forward/k_tc_inverse",
-                                      "peak_src": "measured (MEASURED_PEAKS.json bf16 dense burst)"}
-        elif args.precision == "mixed_tf32":
-            tf = pk["bf16_tflops"] * 0.5  # TF32 dense rate: the BF16 measured peak x the nominal 1.1 / 2.25 ratio
-            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": tf, "unit": "TFLOP/s",
-                                      "frac": a / tf, "kernel": "k_tc_forward/k_tc_inverse (TF32)",
-                                      "peak_src": "measured BF16 peak x nominal TF32/BF16 ratio"}
+        a_t = tc_flops / t["contract"] / 1e12
+        a_b = c_bytes / t["contract"] / 1e9
+        t_tensor, t_hbm = tc_flops / (tc_peak * 1e12), c_bytes / (pk_hbm * 1e9)
+        kern = {"mixed": "k_tc_forward/k_tc_inverse", "mixed_tf32": "k_tc_forward/k_tc_inverse (TF32)"}.get(
+            args.precision, "k_dmma_forward/k_dmma_inverse")
+        tensor = {"achieved": a_t, "peak": tc_peak, "unit": "TFLOP/s", "frac": a_t / tc_peak,
+                  "work": "4 flops per (l, m, m' >= 0, map) multiply-add, both directions",
+                  "peak_src": {"mixed": "measured (MEASURED_PEAKS.json bf16 dense burst)",
+                               "mixed_tf32": "measured BF16 peak x nominal TF32/BF16 ratio"}.get(
+                      args.precision, "measured (own FP64 mma.sync microbenchmark; same FP64 pipe as DFMA)")}
+        hbm = {"achieved": a_b, "peak": pk_hbm, "unit": "GB/s", "frac": a_b / pk_hbm,
+               "work": "staged planes read once per direction, G+ / N_l f_lm read, f_lm / F+ written",
+               "peak_src": pk["src"]}
+        if t_hbm >= t_tensor:
+            stage_roof["contract"] = dict(hbm, bound="hbm", kernel=kern, tensor=tensor)
         else:
-            stage_roof["contract"] = {"bound": "tensor", "achieved": a, "peak": 1.045, "unit": "TFLOP/s",
-                                      "frac": a / 1.045, "kernel": "k_dmma_forward/k_dmma_inverse",
-                                      "peak_src": "measured (own FP64 mma.sync m8n8k4 microbenchmark; "
-                                                  "same FP64 pipe as DFMA on this part)"}
+            stage_roof["contract"] = dict(tensor, bound="tensor", kernel=kern, hbm=hbm)
     for k in ("theta", "phi"):
         if t[k] > 0:
             a = fb[k] / t[k] / 1e9
             stage_roof[k] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
                              "frac": a / pk["hbm_gbs"], "peak_src": pk["src"]}
-    # the Delta stage (recursion + contractions) against max(recursion / FP64,
-    # split tensor products / BF16, plane staging / HBM)
-    staging = sweeps * 4.0 * sum((l + 1) ** 2 for l in range(L)) * (1 + len({s for s in spins}))
-    tc_split = tc_flops * {"mixed": 6, "mixed_tf32": 3}.get(args.precision, 1)
-    tc_peak = {"mixed": pk["bf16_tflops"], "mixed_tf32": pk["bf16_tflops"] * 0.5}.get(args.precision, 1.045)
+    # the Delta stage (recursion + contractions) against the largest of its
+    # floors: the recursion's own (FP64 flops for Risbo in double, FP32 issue or
+    # staging bytes otherwise), the tensor products, and the HBM bytes
     t_d = t["delta"] + t["contract"]
-    bounds_oct = (sweeps * risbo_units(L) * 7 / (pk["fp64_tflops"] * 1e12), tc_split / (tc_peak * 1e12),
-                  staging / (pk["hbm_gbs"] * 1e9))
-    bounds_q = (sweeps * 7.0 * L ** 3 / (pk["fp64_tflops"] * 1e12),) + bounds_oct[1:]
-    delta_stage = {"ms": 1e3 * t_d, "roofline_ms": 1e3 * max(bounds_oct), "frac": max(bounds_oct) / t_d,
-                   "roofline_ms_quarter_plane_units": 1e3 * max(bounds_q), "frac_quarter_plane_units": max(bounds_q) / t_d,
-                   "bounds_ms": {"recursion_fp64": 1e3 * bounds_oct[0], "contraction_tensor": 1e3 * bounds_oct[1],
-                                 "staging_hbm": 1e3 * bounds_oct[2]}}
+    rec_floor = stage_roof["delta"]["floor_ms"] / 1e3 if "delta" in stage_roof else 0.0
+    bounds = (rec_floor, tc_flops / (tc_peak * 1e12), c_bytes / (pk_hbm * 1e9))
+    delta_stage = {"ms": 1e3 * t_d, "roofline_ms": 1e3 * max(bounds), "frac": max(bounds) / t_d,
+                   "recursion": recursion,
+                   "bounds_ms": {"recursion": 1e3 * bounds[0], "contraction_tensor": 1e3 * bounds[1],
+                                 "contraction_hbm": 1e3 * bounds[2]}}
+    if rb_line is not None:
+        rb_line["delta_roofline"] = delta_roofline("risbo_ff", L, rb_line["stage_ms_per_step"]["delta"] / 1e3, pk,
+                                                   fp32_issue, n_sm, mhz)
     dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k])
     if L == 2048 and B == 16 and args.precision == "mixed":
         for k, v in TRAFFIC_L2048_B16.items():
+            if k == "delta" and recursion != "risbo_ff":
+                continue  # captured on the Risbo sweep
             if k in stage_roof:
                 stage_roof[k]["traffic"] = sum(v) / len(v)  # bytes per launch, averaged over the launches
                 stage_roof[k]["traffic_per_step"] = sum(v) * (2 if k == "delta" else 1)
@@ -408,6 +486,7 @@ def run_ours(args, rank, world, local_rank):
         "real": {"value": whole_job_value(world, B, K, r_ms / 1e3), "unit": "transforms/s",
                  "ms_per_step": r_ms / K, "rel_err": r_err,
                  "what": f"round trip of {B} real spin-0 maps (Sec. IV-G), uniform[-1,1] coefficients with the reality condition"},
+        "risbo": rb_line,
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
                 "d2h_bytes_per_step": bytes_map + bytes_flm, "ms_each_step": e2e_each},
         "gpu_launches": launches_per_step * K,

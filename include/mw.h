@@ -99,6 +99,22 @@ enum { MW_FLAG_GRAPH = 1 << 8 };
  * plans reject the flag (MW_EINVAL). */
 enum { MW_FLAG_REAL = 1 << 9 };
 
+/* Recursion of the Wigner planes Delta^l (or-ed into flags; at most one):
+ * MW_FLAG_DELTA_TN     the Trapani-Navaza recursion (cited in Sec. V-B as the
+ *                      alternative to Risbo's).  Each column of each plane
+ *                      recurses independently from the closed-form top row
+ *                      Delta^l_{l,m} = (-1)^(l-m) 2^-l sqrt(C(2l, l+m)), so the
+ *                      planes need no step-by-step synchronisation; each
+ *                      column carries its own power-of-two exponent, which
+ *                      removes the underflow of the start values that limits
+ *                      the recursion in plain double precision (near
+ *                      L = 2560).  Mixed precisions only (MW_EUNSUPPORTED with
+ *                      MW_PREC_FP64).
+ * MW_FLAG_DELTA_RISBO  Risbo's recursion (Sec. V-B), one synchronised sweep.
+ * Neither: Trapani-Navaza on the mixed precisions, Risbo on MW_PREC_FP64.
+ * Both agree to the FP32 staging precision the mixed contractions read. */
+enum { MW_FLAG_DELTA_TN = 1 << 10, MW_FLAG_DELTA_RISBO = 1 << 11 };
+
 /* Create a plan for `batch` maps of band limit L and spin s.
  * Requires 1 <= L <= 2048, |s| < L, batch >= 1, out != NULL.  Allocates the
  * device workspace on the current CUDA device; *out is NULL on failure. */

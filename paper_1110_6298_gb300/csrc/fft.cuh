@@ -10,8 +10,8 @@
 // the inputs of its butterflies, the block synchronises, and the outputs
 // overwrite the inputs, so one shared buffer of n elements suffices.  Other odd
 // primes (the 2L-1 lengths contain factors such as 13, 31, 73 or 127) use a
-// dot-product stage in which each output is an R-term sum; no Bluestein step is
-// needed.  The out-of-place (ping-pong) variant also has register butterflies
+// dot-product stage in which each output is an R-term sum (compensated in
+// FP32); no Bluestein step is needed.  The out-of-place (ping-pong) variant also has register butterflies
 // for 11 and 13 (4095 = 3^2 5 7 13 at L = 2048).  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
 #pragma once
 #include <cuda_runtime.h>
@@ -178,6 +178,21 @@ __device__ __forceinline__ void stage_reg(C<T>* buf, int n, int Ns, const C<T>* 
   __syncthreads();
 }
 
+// Running sum of a dot-product stage.  FP32: compensated (TwoSum of each
+// addition, errors collected separately), so an R-term sum loses no more than
+// its terms' own roundings -- a plain FP32 sum over a large prime radix (a
+// prime 2L-1 such as 599 at L = 300 makes the whole FFT one R-term stage)
+// grows its error with R and costs the mixed path's 1e-6.  FP64: plain sum.
+template <typename T>
+__device__ __forceinline__ void acc_add(T& s, T& c, T x) { s += x; }
+template <>
+__device__ __forceinline__ void acc_add<float>(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float v = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(x, v)));
+  s = t;
+}
+
 // Generic radix stage: every output an R-term dot product (odd primes > 7).
 template <typename T, int VPT>
 __device__ __forceinline__ void stage_dot(C<T>* buf, int n, int Ns, int R, const C<T>* __restrict__ tw, bool inv) {
@@ -189,18 +204,18 @@ __device__ __forceinline__ void stage_dot(C<T>* buf, int n, int Ns, int R, const
     if (o < n) {
       const int om = o % NsR;
       const int j = (o / NsR) * Ns + (o % Ns);
-      T ar = 0, ai = 0;
+      T ar = 0, ai = 0, cr = 0, ci = 0;
       int e = 0;
       for (int r = 0; r < R; ++r) {
         const C<T> x = buf[j + r * stride];
         const C<T> w = tw[e * step];
         const T wi = inv ? -w.y : w.y;
-        ar += x.x * w.x - x.y * wi;
-        ai += x.x * wi + x.y * w.x;
+        acc_add<T>(ar, cr, x.x * w.x - x.y * wi);
+        acc_add<T>(ai, ci, x.x * wi + x.y * w.x);
         e += om;
         if (e >= NsR) e -= NsR;
       }
-      val[v] = mkc<T>(ar, ai);
+      val[v] = mkc<T>(ar + cr, ai + ci);
     }
   }
   __syncthreads();
@@ -269,18 +284,18 @@ __device__ __forceinline__ void stage_dot_pp(const C<T>* __restrict__ in, C<T>* 
   for (int o = threadIdx.x; o < n; o += blockDim.x) {
     const int om = o % NsR;
     const int j = (o / NsR) * Ns + (o % Ns);
-    T ar = 0, ai = 0;
+    T ar = 0, ai = 0, cr = 0, ci = 0;
     int e = 0;
     for (int r = 0; r < R; ++r) {
       const C<T> x = in[j + r * stride];
       const C<T> w = tw[e * step];
       const T wi = inv ? -w.y : w.y;
-      ar += x.x * w.x - x.y * wi;
-      ai += x.x * wi + x.y * w.x;
+      acc_add<T>(ar, cr, x.x * w.x - x.y * wi);
+      acc_add<T>(ai, ci, x.x * wi + x.y * w.x);
       e += om;
       if (e >= NsR) e -= NsR;
     }
-    out[o] = mkc<T>(ar, ai);
+    out[o] = mkc<T>(ar + cr, ai + ci);
   }
   __syncthreads();
 }

@@ -64,6 +64,8 @@ struct mw_plan {
   float2* d_sqrt_ff = nullptr;     // mixed paths: the three tables above as float-float (hi, lo)
   float2* d_rsqrt_ff = nullptr;
   float2* d_rscale_ff = nullptr;
+  float2* d_tn_top = nullptr;      // MW_FLAG_DELTA_TN: top rows Delta^l_{l,m} as float-float mantissas
+  int* d_tn_exp = nullptr;         // and their power-of-two exponents, plane l at l (l + 1) / 2
   double* d_nl = nullptr;          // sqrt((2l+1)/(4 pi)), l < L
   float2* d_flmf = nullptr;        // mixed path: N_l f_lm in FP32 (input of the inverse contraction)
 
@@ -139,6 +141,8 @@ cudaError_t launch_phi_forward_real(const mw_plan* p, const double* maps, cudaSt
 cudaError_t launch_phi_inverse_real(const mw_plan* p, double* maps, cudaStream_t st);
 cudaError_t launch_real_unpack(const mw_plan* p, const double2* g, double2* flm, cudaStream_t st);
 cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, cudaStream_t st);
+// Trapani-Navaza planes l in [lb, le) into staging slots l - l0 (mixed paths)
+cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st);
 
 // Wigner stage: one sweep l = 0..o->L-1 with Risbo's recursion (state of the
 // owner o) and the contractions of the consumer plans cs[0..nc).

@@ -1,0 +1,108 @@
+// kernels_tn.cu -- Delta^l = d^l(pi/2) by the Trapani-Navaza recursion (cited
+// in Sec. V-B as the alternative to Risbo's), for the mixed precisions.
+//
+// Column m of the quarter plane (m' = l .. 0, rows m', columns m) starts from
+// the top row Delta^l_{l,m} = (-1)^(l-m) 2^-l sqrt(C(2l, l+m)) and recurses
+// down the first index with the three-term relation of d^l at beta = pi/2,
+//   sqrt((l+m')(l-m'+1)) Delta_{m'-1,m}
+//     = 2 m Delta_{m',m} - sqrt((l-m')(l+m'+1)) Delta_{m'+1,m},
+// stopping at m' = 0: every step then runs towards growing or oscillating
+// values (the region of |m'| <= sqrt(l^2 - m^2) is where |Delta| is large), so
+// the recursion is stable.  What limits the recursion in double precision is
+// the start values, which fall to about exp(-0.28 l) at m = l / sqrt2 and to
+// 2^-l at m = l and leave the double range near l = 2560.  Here each column
+// carries its own power-of-two exponent: value = x 2^E with x a float-float
+// pair, rescaled by 2^-64 whenever |x| exceeds 2^64, and the start values come
+// from a host table of (float-float mantissa, exponent) pairs.
+//
+// Planes are independent given their top rows, and so are the columns of a
+// plane: one thread per column, one block per (plane, 256 columns), no waits
+// between blocks.  A block first forms the plane's recursion coefficients
+// 2/b(m') and a(m')/b(m') in shared memory (b = sqrt((l+m')(l-m'+1)),
+// a = sqrt((l-m')(l+m'+1))); each step then costs one float-float product by
+// the column index, one product and one multiply-add.  Every step writes one
+// row of the FP32 staging plane, consecutive columns in consecutive threads,
+// so the stores are coalesced and the full quarter is written without a
+// transpose.
+#include <cmath>
+
+#include "ff.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int kTThreads = 256;
+constexpr int kTMaxL = 2048;
+
+struct TnArgs {
+  float* S32;               // FP32 staging: plane l at slot l - l0
+  int l0;
+  int LD;
+  const float2* sq;         // sqrt(k) as float-float
+  const float2* rsq;        // 1/sqrt(k) as float-float
+  const float2* top;        // top-row mantissas, plane l at l (l + 1) / 2
+  const int* top_exp;       // top-row exponents
+};
+
+// x 2^E in single precision (x = the pair's high part)
+__device__ __forceinline__ float scaled(float x, int E) {
+  if (E == 0) return x;
+  if (E < -400) return 0.0f;
+  return ldexpf(x, E);
+}
+
+__global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
+  __shared__ float2 c1[kTMaxL + 1];  // 2 / b(m')
+  __shared__ float2 c2[kTMaxL + 1];  // a(m') / b(m')
+  const int l = lb + (int)blockIdx.y;
+  const int m0 = (int)blockIdx.x * kTThreads;
+  if (m0 > l) return;  // whole block past the plane's last column (uniform)
+  for (int mp = 1 + (int)threadIdx.x; mp <= l; mp += kTThreads) {
+    const float2 ib = NumFF::mul(A.rsq[l + mp], A.rsq[l - mp + 1]);
+    c1[mp] = make_float2(2.0f * ib.x, 2.0f * ib.y);  // exact
+    c2[mp] = NumFF::mul(NumFF::mul(A.sq[l - mp], A.sq[l + mp + 1]), ib);
+  }
+  __syncthreads();
+  const int m = m0 + (int)threadIdx.x;
+  if (m > l) return;
+  const int LD = A.LD;
+  float* st = A.S32 + (size_t)(l - A.l0) * LD * LD + m;
+  const size_t t0 = (size_t)l * (l + 1) / 2 + m;
+  float2 cur = A.top[t0];
+  float2 prev = make_float2(0.f, 0.f);
+  int E = A.top_exp[t0];
+  st[(size_t)l * LD] = scaled(cur.x, E);
+  const float2 mf = make_float2((float)m, 0.f);
+  for (int mp = l; mp >= 1; --mp) {
+    const float2 t = NumFF::mul(c1[mp], mf);    // 2 m / b
+    const float2 u = NumFF::mul(c2[mp], prev);  // (a / b) Delta_{m'+1}
+    const float2 nw = NumFF::fma(t, cur, make_float2(-u.x, -u.y));
+    prev = cur;
+    cur = nw;
+    if (fabsf(cur.x) > 0x1p64f) {  // powers of two scale both parts exactly
+      cur = make_float2(cur.x * 0x1p-64f, cur.y * 0x1p-64f);
+      prev = make_float2(prev.x * 0x1p-64f, prev.y * 0x1p-64f);
+      E += 64;
+    }
+    st[(size_t)(mp - 1) * LD] = scaled(cur.x, E);
+  }
+}
+
+}  // namespace
+
+// Planes l in [lb, le) into the staging slots l - l0 of plan p's sweep state.
+cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st) {
+  if (lb >= le) return cudaSuccess;
+  if (le > kTMaxL) return cudaErrorInvalidValue;
+  TnArgs a;
+  a.S32 = p->d_S32;
+  a.l0 = l0;
+  a.LD = p->LD;
+  a.sq = p->d_sqrt_ff;
+  a.rsq = p->d_rsqrt_ff;
+  a.top = p->d_tn_top;
+  a.top_exp = p->d_tn_exp;
+  const dim3 grid((le - 1) / kTThreads + 1, le - lb);
+  k_tn_planes<<<grid, kTThreads, 0, st>>>(a, lb);
+  return cudaGetLastError();
+}

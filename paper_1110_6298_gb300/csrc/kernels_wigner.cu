@@ -29,6 +29,7 @@
 #include <utility>
 #include <vector>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace {
@@ -76,45 +77,6 @@ struct NumF64 {
   static __device__ __forceinline__ float f32(T v) { return to_f32_int(v); }
 };
 
-// hi + lo from s + e, |s| >= |e| or s + e exact (Fast2Sum)
-__device__ __forceinline__ float2 ff_fast(float s, float e) {
-  const float h = __fadd_rn(s, e);
-  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
-}
-
-struct NumFF {
-  using T = float2;  // (hi, lo)
-  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
-  // a b: TwoProduct of the high parts plus the cross terms (the lo * lo term is
-  // below the format's precision), renormalised
-  static __device__ __forceinline__ T mul(T a, T b) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    return ff_fast(p, e);
-  }
-  // a b + c: TwoProduct of the high parts, TwoSum with c's high part, the
-  // cross terms and both low parts collected, renormalised
-  static __device__ __forceinline__ T fma(T a, T b, T c) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    const float s = __fadd_rn(p, c.x);
-    const float v = __fsub_rn(s, p);
-    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.x, v));
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    e = __fadd_rn(e, __fadd_rn(c.y, err));
-    return ff_fast(s, e);
-  }
-  static __device__ __forceinline__ T fms(T a, T b, T c) { return fma(make_float2(-a.x, -a.y), b, c); }
-  // v (-1)^k: sign bits flipped on the integer pipe
-  static __device__ __forceinline__ T flip(T v, int k) {
-    const unsigned m = (unsigned)(k & 1) << 31;
-    return make_float2(__uint_as_float(__float_as_uint(v.x) ^ m), __uint_as_float(__float_as_uint(v.y) ^ m));
-  }
-  static __device__ __forceinline__ float f32(T v) { return v.x; }  // hi = RN(hi + lo)
-};
 
 // ---------------------------------------------------------------------------
 // Persistent Risbo sweep over the planes l in [l_begin, l_end) of one chunk.
@@ -539,8 +501,13 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     const int l1 = (l0 + chunk < o->L) ? l0 + chunk : o->L;
     StageSpan span_d(o, MW_STAGE_DELTA, st);
     int nd = 0;
-    e = launch_risbo(o, o->d_S, fp64 ? kChunk : 2, fp64 ? nullptr : o->d_S32, l0, fp64 ? 1 : 0, (l0 == 0 ? 1 : l0),
-                     l1, st, &nd);
+    if (o->flags & MW_FLAG_DELTA_TN) {  // Trapani-Navaza: independent planes from their top rows
+      e = launch_tn(o, l0, l0, l1, st);
+      nd = 1;
+    } else {
+      e = launch_risbo(o, o->d_S, fp64 ? kChunk : 2, fp64 ? nullptr : o->d_S32, l0, fp64 ? 1 : 0,
+                       (l0 == 0 ? 1 : l0), l1, st, &nd);
+    }
     if (e != cudaSuccess) return e;
     span_d.end(nd);
     nl += nd;

@@ -69,12 +69,14 @@ void free_plan(mw_plan* p) {
   for (mw_plan* c : p->twins) free_plan(c);
   if (p->shared_sweep) {
     p->d_S = nullptr; p->d_S32 = nullptr; p->d_err = nullptr; p->d_prog = nullptr; p->d_perm = nullptr;
+    p->d_tn_top = nullptr; p->d_tn_exp = nullptr;
   }
   void* ptrs[] = {p->d_groups, p->d_spins, p->d_twM, p->d_twN, p->d_phase, p->d_V, p->d_sqrt, p->d_rsqrt, p->d_upole,
                   p->d_Gt,     p->d_Gp,    p->d_S,   p->d_H,   p->d_map_stage, p->d_flm_stage, p->d_S32, p->d_err,
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
-                  p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff};
+                  p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff,
+                  p->d_tn_top, p->d_tn_exp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -101,7 +103,13 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   if (L < 1 || L > 2048 || B < 1 || !spins) return MW_EINVAL;
   const int prec = (int)(flags & 0xffu);
   if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED && prec != MW_PREC_MIXED_TF32X3) return MW_EINVAL;
-  if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH | (unsigned)MW_FLAG_REAL)) return MW_EINVAL;
+  if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH | (unsigned)MW_FLAG_REAL | (unsigned)MW_FLAG_DELTA_TN |
+                (unsigned)MW_FLAG_DELTA_RISBO))
+    return MW_EINVAL;
+  if ((flags & MW_FLAG_DELTA_TN) && (flags & MW_FLAG_DELTA_RISBO)) return MW_EINVAL;
+  if ((flags & MW_FLAG_DELTA_TN) && prec == MW_PREC_FP64) return MW_EUNSUPPORTED;
+  // default recursion: Trapani-Navaza on the mixed precisions, Risbo on FP64
+  if (!(flags & MW_FLAG_DELTA_RISBO) && prec != MW_PREC_FP64) flags |= MW_FLAG_DELTA_TN;
   for (int b = 0; b < B; ++b)
     if (spins[b] <= -L || spins[b] >= L) return MW_EINVAL;
   // real-signal plans: spin 0 only, caller-contiguous buffers, two real maps per complex map
@@ -295,6 +303,8 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     p->d_err = owner->d_err;
     p->d_prog = owner->d_prog;
     p->d_perm = owner->d_perm;
+    p->d_tn_top = owner->d_tn_top;
+    p->d_tn_exp = owner->d_tn_exp;
     p->risbo_grid = owner->risbo_grid;
   } else {
     const size_t plane = (size_t)p->LD * p->LD;
@@ -305,6 +315,36 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     {
       const int Tm = (L + 1 + 31) / 32;
       alloc((void**)&p->d_prog, sizeof(int) * (size_t)(Tm * (Tm + 1) / 2 + 1));
+    }
+    if (flags & MW_FLAG_DELTA_TN) {
+      // top rows Delta^l_{l,m} = (-1)^(l-m) 2^-l sqrt(C(2l, l+m)) as mantissa * 2^exponent:
+      // Delta^l_{l,l} = 2^-l, and Delta^l_{l,m} = -(1/2) sqrt(2l (2l-1) / ((l+m)(l-m))) Delta^{l-1}_{l-1,m}
+      // for m < l, in long double with the mantissa renormalised after every factor
+      const size_t nt = (size_t)L * (L + 1) / 2;
+      std::vector<float2> tm(nt);
+      std::vector<int> te(nt);
+      std::vector<long double> mt(L);
+      std::vector<int> ex(L);
+      for (int l = 0; l < L; ++l) {
+        for (int m = 0; m < l; ++m) {
+          const long double r2 = (long double)(2 * l) * (2 * l - 1) / ((long double)(l + m) * (l - m));
+          int k = 0;
+          mt[m] = frexpl(mt[m] * (-0.5L * sqrtl(r2)), &k);
+          ex[m] += k;
+        }
+        mt[l] = 0.5L;
+        ex[l] = 1 - l;
+        const size_t t0 = (size_t)l * (l + 1) / 2;
+        for (int m = 0; m <= l; ++m) {
+          const float hi = (float)mt[m];
+          tm[t0 + m] = make_float2(hi, (float)(mt[m] - (long double)hi));
+          te[t0 + m] = ex[m];
+        }
+      }
+      alloc((void**)&p->d_tn_top, sizeof(float2) * nt);
+      if (e == cudaSuccess) chk(cudaMemcpy(p->d_tn_top, tm.data(), sizeof(float2) * nt, cudaMemcpyHostToDevice));
+      alloc((void**)&p->d_tn_exp, sizeof(int) * nt);
+      if (e == cudaSuccess) chk(cudaMemcpy(p->d_tn_exp, te.data(), sizeof(int) * nt, cudaMemcpyHostToDevice));
     }
     if (e == cudaSuccess) {
       int nsm = 0;

@@ -18,6 +18,11 @@ MW_OK, MW_EINVAL, MW_ENOMEM, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = range(6)
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_bf16": 1, "mixed_tf32": 2}
 FLAG_GRAPH = 1 << 8
 FLAG_REAL = 1 << 9
+FLAG_DELTA_TN = 1 << 10
+FLAG_DELTA_RISBO = 1 << 11
+# Wigner-plane recursion: None = the library's default (Trapani-Navaza on the
+# mixed precisions, Risbo on FP64); "tn" (mixed only) or "risbo" to choose
+DELTA = {None: 0, "tn": FLAG_DELTA_TN, "risbo": FLAG_DELTA_RISBO}
 
 _lib = None
 
@@ -116,7 +121,7 @@ def _stream_of(t):
 class Plan:
     """A transform plan: L, one spin per map (or one spin for all), precision."""
 
-    def __init__(self, L, spins, batch=None, precision="fp64", graph=False):
+    def __init__(self, L, spins, batch=None, precision="fp64", graph=False, delta=None):
         if isinstance(spins, int):
             if batch is None:
                 batch = 1
@@ -128,7 +133,7 @@ class Plan:
         self.precision = precision
         h = ctypes.c_void_p()
         arr = (ctypes.c_int * len(spins))(*spins)
-        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0)
+        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0) | DELTA[delta]
         st = lib().mw_plan_create_spins(ctypes.byref(h), self.L, self.batch, arr, flags)
         if st != MW_OK:
             raise MWError(st, "mw_plan_create_spins")
@@ -267,11 +272,11 @@ class RealPlan(Plan):
     a batch of B real maps costs a complex batch of ceil(B/2).  No adjoints or
     quadrature on real plans."""
 
-    def __init__(self, L, batch=1, precision="fp64", graph=False):
+    def __init__(self, L, batch=1, precision="fp64", graph=False, delta=None):
         self.L, self.batch, self.spins = int(L), int(batch), [0] * int(batch)
         self.precision = precision
         h = ctypes.c_void_p()
-        flags = PRECISIONS[precision] | FLAG_REAL | (FLAG_GRAPH if graph else 0)
+        flags = PRECISIONS[precision] | FLAG_REAL | (FLAG_GRAPH if graph else 0) | DELTA[delta]
         st = lib().mw_plan_create(ctypes.byref(h), self.L, 0, self.batch, flags)
         if st != MW_OK:
             raise MWError(st, "mw_plan_create (real)")
@@ -345,7 +350,7 @@ class RaggedPlan(Plan):
 
     _uniform = False
 
-    def __init__(self, Ls, spins, precision="mixed", graph=False):
+    def __init__(self, Ls, spins, precision="mixed", graph=False, delta=None):
         Ls = [int(x) for x in Ls]
         spins = [int(x) for x in spins]
         if len(Ls) != len(spins):
@@ -355,7 +360,7 @@ class RaggedPlan(Plan):
         h = ctypes.c_void_p()
         la = (ctypes.c_int * len(Ls))(*Ls)
         sa = (ctypes.c_int * len(spins))(*spins)
-        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0)
+        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0) | DELTA[delta]
         st = lib().mw_plan_create_ragged(ctypes.byref(h), len(Ls), la, sa, flags)
         if st != MW_OK:
             raise MWError(st, "mw_plan_create_ragged")
