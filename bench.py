@@ -224,6 +224,21 @@ def delta_roofline(recursion, L, seconds, pk, fp32_issue, n_sm, mhz):
     return out
 
 
+def survey_delta_stage(L, t_d, fp64_tflops, tc_flops, tc_peak, c_bytes, hbm_gbs):
+    """The Delta stage (recursion + contractions, t_d seconds per round trip)
+    against the formula that counts the recursion at the FP64 rate: max(7
+    flops per element of two recursions / FP64 peak, products / tensor peak,
+    bytes / HBM), with the recursion's elements counted as the octant that
+    the pi/2 symmetries leave and, second, as L^3 per sweep (quarter plane)."""
+    sweeps = 2
+    rec_oct = sweeps * risbo_units(L) * 7 / (fp64_tflops * 1e12)
+    rec_q = sweeps * 7.0 * L ** 3 / (fp64_tflops * 1e12)
+    rest = max(tc_flops / (tc_peak * 1e12), c_bytes / (hbm_gbs * 1e9))
+    return {"frac": max(rec_oct, rest) / t_d, "frac_quarter_plane_units": max(rec_q, rest) / t_d,
+            "roofline_ms": 1e3 * max(rec_oct, rest), "roofline_ms_quarter_plane_units": 1e3 * max(rec_q, rest),
+            "what": "recursion counted at the FP64 rate (7 flops per element) whatever arithmetic runs it"}
+
+
 def fft_stage_bytes(L, B, precision):
     """Algorithmic HBM bytes of the FFT stages of one round trip (inverse +
     forward): every stage boundary written once and read once."""
@@ -449,7 +464,9 @@ def run_ours(args, rank, world, local_rank):
     delta_stage = {"ms": 1e3 * t_d, "roofline_ms": 1e3 * max(bounds), "frac": max(bounds) / t_d,
                    "recursion": recursion,
                    "bounds_ms": {"recursion": 1e3 * bounds[0], "contraction_tensor": 1e3 * bounds[1],
-                                 "contraction_hbm": 1e3 * bounds[2]}}
+                                 "contraction_hbm": 1e3 * bounds[2]},
+                   "fp64_rate_formula": survey_delta_stage(L, t_d, pk["fp64_tflops"], tc_flops, tc_peak, c_bytes,
+                                                           pk_hbm)}
     if rb_line is not None:
         rb_line["delta_roofline"] = delta_roofline("risbo_ff", L, rb_line["stage_ms_per_step"]["delta"] / 1e3, pk,
                                                    fp32_issue, n_sm, mhz)
