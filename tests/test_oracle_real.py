@@ -11,7 +11,10 @@
   coefficients (not only those of a real signal);
 - exact round trip on real band-limited maps;
 - planted mistakes (the (-1)^m of the reality condition dropped, the conjugate
-  dropped) are caught.
+  dropped) are caught;
+- the general reality condition for spin signals: conj of a spin-s signal is a
+  spin -s signal with coefficients (-1)^(s+m) conj(f_{l,-m}), through both
+  transforms of the complex path at s = 1, 2, -3, 4.
 """
 import numpy as np
 import pytest
@@ -109,3 +112,19 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(oracle.mw_oracle, "hermitian_part",
                         lambda x, L_: 0.5 * (x + oracle.mw_oracle._neg_m_sign(L_) * x[..., oracle.mw_oracle._mirror_index(L_)]))
     assert np.max(np.abs(oracle.inverse_real(c, L) - good)) > 0.1
+
+
+@pytest.mark.parametrize("L,s", [(4, 1), (6, 2), (7, -3), (5, 4)])
+def test_spin_reality_condition(L, s):
+    # Sec. IV-G: for a spin-s signal f, conj(f) is a spin -s signal with
+    # coefficients (-1)^(s+m) conj(f_{l,-m}); checked through both transforms
+    flm = wl.uniform_flm(wl.rng(750 + L), L, s)
+    f = oracle.inverse(flm, L, s)
+    g = oracle.forward(np.conj(f), L, -s)
+    ell = wl.ell_of_index(L)
+    m = np.arange(L * L) - ell * ell - ell
+    mirror = ell * ell + ell - m
+    want = np.where((s + m) % 2 == 0, 1.0, -1.0) * np.conj(flm[mirror])
+    assert np.max(np.abs(g - want)) < 1e-12
+    # and the synthesis side: inverse of those coefficients with spin -s is conj(f)
+    assert np.max(np.abs(oracle.inverse(want, L, -s) - np.conj(f))) < 1e-12
