@@ -126,3 +126,25 @@ def brute_force_inverse(flm, L, s):
     out[: (L - 1) * M] = rings[: L - 1].ravel()
     out[(L - 1) * M] = rings[L - 1, 0]
     return out
+
+
+def delta_half_pi_exact(l, m, n):
+    """d^l_{mn}(pi/2) for integer l from Wigner's explicit sum (d_sum) at
+    cos = sin = 1/sqrt2: with the terms regrouped into binomials,
+      d^l_{mn}(pi/2) = 2^-l sqrt((l+m)!(l-m)! / ((l+n)!(l-n)!))
+                       * sum_k (-1)^(k-n+m) C(l+n, k) C(l-n, k-n+m),
+    whose sum is an exact integer; only the final square root of an exact
+    rational is rounded (40 digits)."""
+    from math import comb, factorial
+    T = 0
+    for k in range(0, l + n + 1):
+        j = k - n + m
+        if 0 <= j <= l - n:
+            T += (-1) ** (j % 2) * comb(l + n, k) * comb(l - n, j)
+    if T == 0:
+        return mp.mpf(0)
+    num = T * T * factorial(l + m) * factorial(l - m)
+    den = factorial(l + n) * factorial(l - n) * 4 ** l
+    with mp.workdps(40):
+        v = mp.sqrt(mp.mpf(num) / mp.mpf(den))
+    return v if T > 0 else -v

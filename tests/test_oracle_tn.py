@@ -9,6 +9,9 @@ recursion) and of the top row it starts from.
 - the transpose symmetry Delta_{m',m} = (-1)^(m-m') Delta_{m,m'} (Eq.
   wignerd_sym3 with d(-b) = d(b)^T), which the column recursion does not
   impose: each triangle is computed from different start values;
+- spot values at l = 2047 (and of Risbo's planes at l = 511) against Wigner's
+  explicit sum evaluated exactly in integers (inside, on and outside the
+  circle m^2 + m'^2 = l^2, and at 2^-2047);
 - planted mistakes (the sign of the 2m term, a dropped factor of the
   recursion, an exponent off by one in the start values) are caught.
 """
@@ -17,7 +20,7 @@ import numpy as np
 import pytest
 
 import oracle
-from exact_wigner import delta_exact
+from exact_wigner import delta_exact, delta_half_pi_exact
 
 
 @pytest.mark.parametrize("l", [0, 1, 2, 5, 12])
@@ -81,3 +84,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
             prev, cur = cur, (s1 * 2.0 * m * cur - a * prev) / b
             out[mp_ - 1] = cur
         assert np.max(np.abs(out - ref)) > 1e-3, mistake
+
+
+SPOTS = [(1, 0), (0, 1), (1000, 500), (500, 1000), (1447, 1447), (2047, 0), (2047, 2047), (1800, 300),
+         (2046, 500), (100, 1999), (0, 0)]
+
+
+def recursion_bound(l, D):
+    """Worst-case rounding of a recursion of up to 2l dependent steps, each
+    rounding at most one unit in the last place of the plane's largest
+    entries: 2 l eps max|Delta| (observed errors sit 10 to 50 times below)."""
+    return 2 * l * np.finfo(np.float64).eps * np.max(np.abs(D))
+
+
+def test_spot_values_at_l2047():
+    l = 2047
+    Q = oracle.delta_plane_tn(l)
+    tol = recursion_bound(l, Q)
+    for a, b in SPOTS:
+        assert abs(Q[a, b] - float(delta_half_pi_exact(l, a, b))) < tol, (a, b)
+
+
+def test_risbo_spot_values_at_l511():
+    l = 511
+    D = oracle.delta_plane(l)
+    tol = recursion_bound(l, D)
+    for a, b in [(0, 1), (300, 200), (361, 361), (511, 0), (510, 100), (20, 499), (-7, 400), (250, -250)]:
+        assert abs(D[a + l, b + l] - float(delta_half_pi_exact(l, a, b))) < tol, (a, b)
