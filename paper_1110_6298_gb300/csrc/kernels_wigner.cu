@@ -61,7 +61,7 @@ __device__ __forceinline__ float to_f32_int(double v) {
 // two floats with |lo| <= ulp(hi) / 2 (about 48 significant bits), built from
 // the error-free transformations TwoSum (Knuth) and TwoProduct by FMA
 // (Dekker's product with a fused multiply-add), so the stencil runs on the FP32
-// pipe, which is about 80 times faster than the FP64 pipe on this part.  The
+// pipe, which is about 68 times faster than the FP64 pipe on this part.  The
 // planes feed an FP32 staging copy and a contraction designed for 1e-6, so 48
 // bits leave a margin of about five orders of magnitude over the 2L half steps.
 // The _rn intrinsics keep the compiler from contracting a product into the
