@@ -58,3 +58,49 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mw, "LIB_PATH", str(tmp_path / "libmw.so"))
     with pytest.raises(RuntimeError):
         mw.lib()
+
+
+def header_constants():
+    """name -> value of the enum constants of include/mw.h (integers and 1 << k)."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mw.h")).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", src):
+        for item in body.split(","):
+            m = re.match(r"\s*(MW_[A-Z0-9_]+)\s*=\s*(.+?)\s*$", item)
+            if m:
+                expr = m.group(2)
+                if re.fullmatch(r"[0-9<\s]+", expr):
+                    out[m.group(1)] = eval(expr)  # integer literals and shifts only
+    return out
+
+
+def test_binding_constants_match_header():
+    import paper_1110_6298_gb300.mw as mw
+    c = header_constants()
+    assert c["MW_FLAG_GRAPH"] == mw.FLAG_GRAPH
+    assert c["MW_FLAG_REAL"] == mw.FLAG_REAL
+    assert c["MW_FLAG_DELTA_TN"] == mw.FLAG_DELTA_TN == mw.DELTA["tn"]
+    assert c["MW_FLAG_DELTA_RISBO"] == mw.FLAG_DELTA_RISBO == mw.DELTA["risbo"]
+    assert c["MW_PREC_FP64"] == mw.PRECISIONS["fp64"]
+    assert c["MW_PREC_MIXED_BF16X3"] == mw.PRECISIONS["mixed"] == mw.PRECISIONS["mixed_bf16"]
+    assert c["MW_PREC_MIXED_TF32X3"] == mw.PRECISIONS["mixed_tf32"]
+    assert (c["MW_OK"], c["MW_EINVAL"], c["MW_EUNSUPPORTED"]) == (mw.MW_OK, mw.MW_EINVAL, mw.MW_EUNSUPPORTED)
+
+
+def test_flag_rules_checked_before_device_work(libmw):
+    c = header_constants()
+    h = ctypes.c_void_p()
+    tn, rb, real = c["MW_FLAG_DELTA_TN"], c["MW_FLAG_DELTA_RISBO"], c["MW_FLAG_REAL"]
+    mixed, fp64 = c["MW_PREC_MIXED"], c["MW_PREC_FP64"]
+    # both recursions at once
+    assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, mixed | tn | rb) == c["MW_EINVAL"]
+    # Trapani-Navaza is for the mixed precisions only
+    assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, fp64 | tn) == c["MW_EUNSUPPORTED"]
+    # real-signal plans are spin 0 and not ragged
+    assert libmw.mw_plan_create(ctypes.byref(h), 8, 1, 2, mixed | real) == c["MW_EINVAL"]
+    Ls = (ctypes.c_int * 2)(8, 4)
+    ss = (ctypes.c_int * 2)(0, 0)
+    assert libmw.mw_plan_create_ragged(ctypes.byref(h), 2, Ls, ss, mixed | real) == c["MW_EINVAL"]
+    # an unknown flag bit
+    assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, mixed | (1 << 12)) == c["MW_EINVAL"]
+    assert not h.value
