@@ -163,6 +163,28 @@ def risbo_ff_instructions(L):
     return tot
 
 
+def error_report(x, ref, L, n_bands=8):
+    """Relative errors of f_lm tensors [B][L*L] (any device): rel_max =
+    max|x - ref| / max|ref|, rel_rms = ||x - ref|| / ||ref||, and rel_max per
+    band of l (n_bands equal bands of l, each relative to the band's own
+    max|ref|), as floats."""
+    import torch
+    d = (x - ref).abs().reshape(-1, L * L).to(torch.float64)
+    r = ref.abs().reshape(-1, L * L).to(torch.float64)
+    out = {"rel_max": float(d.max() / r.max().clamp_min(1e-300)),
+           "rel_rms": float(d.norm() / r.norm().clamp_min(1e-300))}
+    ell = torch.arange(L * L, device=d.device, dtype=torch.float64).sqrt().floor().to(torch.int64)
+    edges = [round(k * L / n_bands) for k in range(n_bands + 1)]
+    bands = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        if hi <= lo:
+            continue
+        sel = (ell >= lo) & (ell < hi)
+        bands.append({"l": [lo, hi], "rel_max": float(d[:, sel].max() / r[:, sel].max().clamp_min(1e-300))})
+    out["bands"] = bands
+    return out
+
+
 def tn_units(L):
     """Quarter-plane elements of one Trapani-Navaza pass over the planes
     l < L: every column m of plane l recurses over m' = l .. 0."""
@@ -300,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     plan.sync()
     err = float((out - flm).abs().max().item() / flm.abs().max().item())
+    err_report = error_report(out, flm, L)
 
     # the timed round trips (graph replays), clocks sampled meanwhile
     clocks = ClockSampler(local_rank)
@@ -491,6 +514,7 @@ def run_ours(args, rank, world, local_rank):
                    "L": L, "batch": B, "spins": spins, "precision": args.precision,
                    "l2_flush": "inputs larger than L2", "graph": True, "parallelism": f"replicas x{world}"},
         "roundtrip_rel_err": err,
+        "roundtrip_errors": err_report,
         "forward_rate": whole_job_value(world, B, K, fwd_ms / 1e3) / 2,
         "inverse_rate": whole_job_value(world, B, K, inv_ms / 1e3) / 2,
         "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",

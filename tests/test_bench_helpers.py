@@ -64,3 +64,26 @@ def test_survey_formula_and_job_value():
     assert r["frac_quarter_plane_units"] > r["frac"]
     # whole-job transforms/s: 2 B transforms per rank and step
     assert bench.whole_job_value(2, 16, 10, 1.0) == 2 * 2 * 16 * 10
+
+
+def test_error_report_on_host_tensors():
+    torch = pytest.importorskip("torch")
+    L = 16
+    g = torch.Generator().manual_seed(0)
+    ref = torch.randn(3, L * L, dtype=torch.complex128, generator=g)
+    x = ref.clone()
+    # perturb one coefficient in band l = 9 (index l*l + l + m)
+    x[1, 9 * 9 + 9 + 2] += 1e-3
+    rep = bench.error_report(x, ref, L, n_bands=4)
+    assert abs(rep["rel_max"] - 1e-3 / float(ref.abs().max())) < 1e-12
+    assert abs(rep["rel_rms"] - 1e-3 / float(ref.norm())) < 1e-12
+    assert [b["l"] for b in rep["bands"]] == [[0, 4], [4, 8], [8, 12], [12, 16]]
+    for b in rep["bands"]:
+        if b["l"] == [8, 12]:
+            sel = torch.tensor([8 <= int(i ** 0.5) < 12 for i in range(L * L)])
+            assert abs(b["rel_max"] - 1e-3 / float(ref[:, sel].abs().max())) < 1e-12
+        else:
+            assert b["rel_max"] == 0.0
+    # exact copies give zeros everywhere
+    z = bench.error_report(ref, ref, L)
+    assert z["rel_max"] == 0.0 and z["rel_rms"] == 0.0 and all(b["rel_max"] == 0.0 for b in z["bands"])
