@@ -64,8 +64,10 @@ typedef enum {
 
 /* Precision of a plan (flags & 0xff).
  * MW_PREC_FP64 : every stage in IEEE double.
- * MW_PREC_MIXED (= MW_PREC_MIXED_BF16X3): the Wigner-Delta recursion (Risbo,
- *                Sec. V-B) in double; the Delta contraction on the tensor cores
+ * MW_PREC_MIXED (= MW_PREC_MIXED_BF16X3): the Wigner-Delta recursion (Sec. V-B;
+ *                Trapani-Navaza by default, Risbo's on request, see below) in
+ *                float-float arithmetic (about 48 significant bits) on the FP32
+ *                pipe; the Delta contraction on the tensor cores
  *                (tcgen05) with FP32 operands split into three BF16 parts (six
  *                products), FP32 accumulation and a float-float sum across
  *                K tiles and chunks; the FFT stages in single precision.
@@ -217,7 +219,7 @@ int mw_plan_last_launches(const mw_plan *plan);
  *   MW_STAGE_PHI     phi DFTs (and their adjoints); on real plans also the
  *                    f_lm pack / unpack of the map pairs
  *   MW_STAGE_THETA   theta extension / DFT / weight convolution (and adjoints)
- *   MW_STAGE_DELTA   Risbo recursion of the Wigner-Delta planes
+ *   MW_STAGE_DELTA   recursion of the Wigner-Delta planes (Risbo or Trapani-Navaza)
  *   MW_STAGE_CONTRACT Delta contraction (forward or inverse sum)
  * mw_plan_stage_times waits for the recorded events, adds their durations to
  * running totals and returns them: ms[MW_NUM_STAGES] milliseconds and

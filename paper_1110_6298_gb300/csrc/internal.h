@@ -144,8 +144,9 @@ cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, c
 // Trapani-Navaza planes l in [lb, le) into staging slots l - l0 (mixed paths)
 cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st);
 
-// Wigner stage: one sweep l = 0..o->L-1 with Risbo's recursion (state of the
-// owner o) and the contractions of the consumer plans cs[0..nc).
+// Wigner stage: one pass l = 0..o->L-1 over the planes of the owner o (Risbo's
+// sweep or the Trapani-Navaza planes, by o's flags) and the contractions of
+// the consumer plans.
 // mode 0: f_lm from G+ (Eq. flm_wig); mode 1: F+ from f_lm (Eq. Fmm).
 int risbo_blocks_per_sm(int prec);
 int quad_chunks(const mw_plan* p);

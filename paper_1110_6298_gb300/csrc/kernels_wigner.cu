@@ -474,8 +474,9 @@ cudaError_t launch_risbo(mw_plan* p, void* S, int nslot, float* S32, int l0, int
   return e;
 }
 
-// One Risbo sweep (recursion state and staging of the owner o) feeding the
-// contractions of the jobs: for a regular plan one job on o itself; for a
+// One pass over the planes (Risbo's sweep, or the Trapani-Navaza planes when
+// the owner's flags ask for them; recursion state and staging of the owner o)
+// feeding the contractions of the jobs: for a regular plan one job on o itself; for a
 // ragged plan one per band-limit sub-plan; for a fused forward+inverse call
 // the forward jobs and the inverse jobs together.  Plane l serves every job
 // with L > l: Delta^l depends on neither L nor s.
