@@ -37,13 +37,10 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# stage kernels at L = 2048, B = 16, mixed, from one 1-pass ncu capture of
-# this bench (the kernels unchanged since): the sweep's four 512-plane chunks
-# and the contraction's four chunks per direction; None where not captured.
-TRAFFIC_L2048_B16 = {
-    "delta": [0.126e9, 1.221e9, 3.447e9, 8.202e9],
-    "contract": [0.746e9, 4.946e9, 12.671e9, 23.986e9, 0.454e9, 3.526e9, 9.264e9, 17.619e9],
-}
+# stage kernels, keyed by (L, B, precision), from a 1-pass ncu capture of this
+# bench's round trip with the kernels as they are now (the capture command is
+# given beside the figures in profiles/); a stage absent here reports null.
+TRAFFIC = {}
 
 
 def peaks():
@@ -55,10 +52,37 @@ def peaks():
         pk["src"] = "measured"
     except Exception:
         pass
-    # FP64 CUDA-core FMA peak: own DFMA microbenchmark on this machine's GB300
-    # (profiles/gb300_fp64_peaks.md); no FP64 entry exists in MEASURED_PEAKS.json.
+    # FP64 peak: MEASURED_PEAKS.json has no FP64 entry; the figure is this
+    # part's FP64 DFMA rate from an own microbenchmark, replaced by a DGEMM
+    # measured in the same run when fp64_peak_live() succeeds.
     pk["fp64_tflops"] = 0.993
+    pk["fp64_src"] = "own DFMA microbenchmark (constant)"
     return pk
+
+
+def fp64_peak_live(dev):
+    """FP64 throughput of torch.matmul (cuBLAS DGEMM, 4096^3, best of 3 after a
+    warm-up) on this GPU, in TFLOP/s; None if it fails."""
+    try:
+        import torch
+        n = 4096
+        a = torch.randn(n, n, dtype=torch.float64, device=dev)
+        b = torch.randn(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(a, b)
+        torch.cuda.synchronize(dev)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -231,7 +255,7 @@ def delta_roofline(recursion, L, seconds, pk, fp32_issue, n_sm, mhz):
     a = fl / seconds / 1e12
     out = {"bound": "alu", "achieved": a, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
            "frac": a / pk["fp64_tflops"], "kernel": "k_risbo_sweep", "recursion": "Risbo",
-           "peak_src": "measured (own FP64 DFMA microbenchmark)",
+           "peak_src": pk.get("fp64_src", "own FP64 DFMA microbenchmark"),
            "work": "7 flops per octant element of each half-step plane",
            "frac_quarter_plane_units": sweeps * 7.0 * L ** 3 / seconds / 1e12 / pk["fp64_tflops"],
            "floor_ms": 1e3 * fl / (pk["fp64_tflops"] * 1e12)}
@@ -273,6 +297,45 @@ def fft_stage_bytes(L, B, precision):
     return {"phi": phi, "theta": theta}
 
 
+def timed_calls(fn, n, stream, dev):
+    """n calls of fn bracketed by barriers and device syncs, CUDA events on the
+    call stream around each; returns (total ms, max over ranks; per-call ms)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    rank_barrier()
+    torch.cuda.synchronize(dev)
+    for i in range(n):
+        ev[i].record(stream)
+        fn()
+    ev[n].record(stream)
+    torch.cuda.synchronize(dev)
+    rank_barrier()
+    each = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+    return rank_max(ev[0].elapsed_time(ev[n]), dev), each
+
+
+def rel_errors(x, ref):
+    """rel_max = max|x - ref| / max|ref| and rel_rms = ||x - ref|| / ||ref||."""
+    d = (x - ref).abs()
+    return {"rel_max": float(d.max() / ref.abs().max().clamp_min(1e-300)),
+            "rel_rms": float(d.norm() / ref.abs().norm().clamp_min(1e-300))}
+
+
+def stage_breakdown(plan, call, n, dev):
+    """Per-stage milliseconds per call (the library's stage events, graphs off)
+    and kernel launches per call."""
+    import torch
+    plan.set_timing(True)
+    plan.stage_times(reset=True)
+    nl = 0
+    for _ in range(n):
+        nl = call()
+    torch.cuda.synchronize(dev)
+    st = {k: v[0] / n for k, v in plan.stage_times(reset=True).items()}
+    plan.set_timing(False)
+    return st, nl
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -291,66 +354,80 @@ def run_ours(args, rank, world, local_rank):
     nmw = mw.map_size(L)
     flm_h = torch.from_numpy(np.stack(w["flm"]))
     flm = flm_h.to(dev)
-    # whole calls are captured as CUDA graphs on first use and replayed
+    stream = torch.cuda.current_stream(dev)
+    K, W = args.steps, args.warmup
+    timed = lambda fn, n: timed_calls(fn, n, stream, dev)  # noqa: E731
+
+    def roundtrip_arm(plan, out_maps, out_flm):
+        """Warm up, then time K graph-replayed round trips (inverse of the
+        batch, forward of the result) of `plan`."""
+        def rt():
+            plan.inverse(flm, out=out_maps)
+            plan.forward(out_maps, out=out_flm)
+        for _ in range(W):
+            rt()
+        torch.cuda.synchronize(dev)
+        plan.sync()
+        return timed(rt, K)
+
+    def breakdown(plan, out_maps, out_flm):
+        def call():
+            plan.inverse(flm, out=out_maps)
+            n = plan.last_launches
+            plan.forward(out_maps, out=out_flm)
+            return n + plan.last_launches
+        return stage_breakdown(plan, call, 2, dev)
+
+    # ---- the headline: mixed precision, whole calls replayed as CUDA graphs
     plan = mw.Plan(L, spins, precision=args.precision, graph=True)
     maps = torch.empty((B, nmw), dtype=torch.complex128, device=dev)
     out = torch.empty_like(flm)
-    stream = torch.cuda.current_stream(dev)
-    K = args.steps
-
-    def roundtrip():
-        plan.inverse(flm, out=maps)
-        plan.forward(maps, out=out)
-
-    def timed(fn, n):
-        """n calls of fn bracketed by barriers and syncs; CUDA events on the
-        call stream around each; returns (total ms max over ranks, per-call ms)."""
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
-        rank_barrier()
-        torch.cuda.synchronize(dev)
-        for i in range(n):
-            ev[i].record(stream)
-            fn()
-        ev[n].record(stream)
-        torch.cuda.synchronize(dev)
-        rank_barrier()
-        each = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
-        return rank_max(ev[0].elapsed_time(ev[n]), dev), each
-
-    for _ in range(args.warmup):
-        roundtrip()
-    torch.cuda.synchronize(dev)
-    plan.sync()
-    err = float((out - flm).abs().max().item() / flm.abs().max().item())
-    err_report = error_report(out, flm, L)
-
-    # the timed round trips (graph replays), clocks sampled meanwhile
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ms, each = timed(roundtrip, K)
+    ms, each = roundtrip_arm(plan, maps, out)
     ck = clocks.stop()
     value = whole_job_value(world, B, K, ms / 1e3)
+    err_report = error_report(out, flm, L)
+    stages, launches_per_step = breakdown(plan, maps, out)
 
-    # per-stage breakdown and kernel count: the same round trip run directly
-    # (per-stage CUDA events on the call stream; graphs are not used meanwhile)
-    plan.set_timing(True)
-    plan.stage_times(reset=True)
-    n_bd = 2
-    launches_per_step = 0
-    for _ in range(n_bd):
+    # ---- the plain FP64 GPU path on the identical workload and protocol
+    fp64_line = None
+    acc = {}
+    if args.precision != "fp64" and not args.no_fp64_arm:
+        p64 = mw.Plan(L, spins, precision="fp64", graph=True)
+        maps64 = torch.empty_like(maps)
+        out64 = torch.empty_like(out)
+        ms64, each64 = roundtrip_arm(p64, maps64, out64)
+        st64, _ = breakdown(p64, maps64, out64)
+        v64 = whole_job_value(world, B, K, ms64 / 1e3)
+        # the mixed path against the FP64 path (itself pinned to the FP64
+        # oracle at 1e-12) on every output: the inverse of the batch, and the
+        # forward of the FP64 maps, per band of l
         plan.inverse(flm, out=maps)
-        n_inv = plan.last_launches
-        plan.forward(maps, out=out)
-        launches_per_step = n_inv + plan.last_launches
+        acc["inverse_vs_fp64"] = rel_errors(maps, maps64)
+        fm = torch.empty_like(out)
+        plan.forward(maps64, out=fm)
+        p64.forward(maps64, out=out64)
+        acc["forward_vs_fp64"] = error_report(fm, out64, L)
+        p64.inverse(flm, out=maps64)
+        p64.forward(maps64, out=out64)
+        rt64 = error_report(out64, flm, L)
+        p64.close()
+        del p64, maps64, out64, fm
+        fp64_line = {"value": v64, "unit": "transforms/s", "ms_per_step": ms64 / K,
+                     "ms_per_step_median": statistics.median(each64), "steps": K, "warmup": W,
+                     "roundtrip_rel_max": rt64["rel_max"], "roundtrip_rel_rms": rt64["rel_rms"],
+                     "stage_ms_per_step": st64,
+                     "what": "the same round trip on an MW_PREC_FP64 plan (FP64 FFTs, FP64 Risbo sweep, "
+                             "DMMA contraction), graph-replayed, CUDA events, same steps"}
     torch.cuda.synchronize(dev)
-    stages = {k: v[0] / n_bd for k, v in plan.stage_times(reset=True).items()}
-    plan.set_timing(False)
 
-    # separate forward and inverse rates
+    # ---- separate forward and inverse rates
     inv_ms, _ = timed(lambda: plan.inverse(flm, out=maps), K)
     fwd_ms, _ = timed(lambda: plan.forward(maps, out=out), K)
+    plan.forward(maps, out=out)
 
-    # fused forward + inverse of independent batches (one shared recursion)
+    # ---- fused forward + inverse of independent batches (one shared recursion)
     flm2 = torch.from_numpy(np.stack(wl.workload_l2048_b16(L=args.L, seed=14)["flm"])).to(dev)
     maps_in = plan.inverse(flm2)
     fu_flm, fu_map = torch.empty_like(flm), torch.empty_like(maps)
@@ -359,20 +436,17 @@ def run_ours(args, rank, world, local_rank):
     fu_err = float((fu_flm - flm2).abs().max().item() / flm2.abs().max().item())
     del flm2, maps_in, fu_flm, fu_map
 
-    # quadrature rule (Sec. IV-F): integrals of B maps in the quadrature layout
+    # ---- quadrature rule (Sec. IV-F): integrals of B maps in the quadrature layout
     gq = torch.Generator(device=dev)
     gq.manual_seed(11106298)
     mq = torch.randn((B, mw.quadrature_size(L)), dtype=torch.complex128, device=dev, generator=gq)
     qout = torch.empty(B, dtype=torch.complex128, device=dev)
     plan.quadrature(mq, out=qout)
     q_ms, _ = timed(lambda: plan.quadrature(mq, out=qout), K)
-    q_bytes = mq.numel() * 16
-    q_gbs = q_bytes * K / (q_ms / 1e3) / 1e9
+    q_gbs = mq.numel() * 16 * K / (q_ms / 1e3) / 1e9
     del mq
 
-    # real signals (Sec. IV-G): the round trip of B real spin-0 maps (two per
-    # complex transform inside the library), coefficients with the reality
-    # condition drawn as in the paper's accuracy protocol
+    # ---- real signals (Sec. IV-G): B real spin-0 maps, two per complex transform
     rplan = mw.RealPlan(L, B, precision=args.precision, graph=True)
     cr = torch.from_numpy(np.stack([wl.uniform_flm_real(wl.rng(3300 + b), L) for b in range(B)])).to(dev)
     rmap = torch.empty((B, nmw), dtype=torch.float64, device=dev)
@@ -390,58 +464,53 @@ def run_ours(args, rank, world, local_rank):
     rplan.close()
     del rplan, cr, rmap, rout
 
-    # the same round trip with Risbo's recursion for the Wigner planes (the
-    # mixed plans' default is the Trapani-Navaza recursion)
+    # ---- the same round trip with Risbo's recursion for the Wigner planes
     rb_line = None
     if args.precision != "fp64":
         rb = mw.Plan(L, spins, precision=args.precision, graph=True, delta="risbo")
         rb_out = torch.empty_like(flm)
-
-        def risbo_roundtrip():
-            rb.inverse(flm, out=maps)
-            rb.forward(maps, out=rb_out)
-
-        for _ in range(2):
-            risbo_roundtrip()
-        rb.sync()
+        rb_ms, _ = roundtrip_arm(rb, maps, rb_out)
         rb_err = float((rb_out - flm).abs().max().item() / flm.abs().max().item())
-        rb_ms, _ = timed(risbo_roundtrip, K)
-        rb.set_timing(True)
-        rb.stage_times(reset=True)
-        rb.inverse(flm, out=maps)
-        rb.forward(maps, out=rb_out)
-        torch.cuda.synchronize(dev)
-        rb_stages = {k: v[0] for k, v in rb.stage_times(reset=True).items()}
+        rb_stages, _ = breakdown(rb, maps, rb_out)
         rb.close()
         del rb, rb_out
         rb_line = {"value": whole_job_value(world, B, K, rb_ms / 1e3), "unit": "transforms/s",
                    "ms_per_step": rb_ms / K, "rel_err": rb_err, "stage_ms_per_step": rb_stages,
                    "what": "the same round trip with Risbo's recursion (MW_FLAG_DELTA_RISBO)"}
 
-    # end to end: the round trip through the C ABI with pinned host buffers,
-    # host<->device copies inside the timed region
+    # ---- end to end: the round trip through the C ABI with pinned host
+    # buffers, host<->device copies inside the timed region, every step
     flm_pin = flm_h.pin_memory()
     map_pin = torch.empty((B, nmw), dtype=torch.complex128).pin_memory()
     out_pin = torch.empty_like(flm_pin).pin_memory()
-    e2e_steps = max(1, min(K, 3))
     plan.inverse(flm_pin, out=map_pin)
     plan.forward(map_pin, out=out_pin)
     rank_barrier()
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     e2e_each = []
-    for _ in range(e2e_steps):
+    for _ in range(K):
         ts = time.perf_counter()
         plan.inverse(flm_pin, out=map_pin)
         plan.forward(map_pin, out=out_pin)
         e2e_each.append(1e3 * (time.perf_counter() - ts))
     torch.cuda.synchronize(dev)
     t_e2e = rank_max(time.perf_counter() - t0, dev)
-    e2e_value = whole_job_value(world, B, e2e_steps, t_e2e)
+    e2e_value = whole_job_value(world, B, K, t_e2e)
     bytes_flm = B * L * L * 16
     bytes_map = B * nmw * 16
+    e2e_err = float((out_pin - flm_h).abs().max() / flm_h.abs().max())
+    del flm_pin, map_pin, out_pin
 
-    # rooflines per round trip: every stage against its own bound
+    # ---- the other configurations and the paper's accuracy protocol
+    configs = None if args.no_configs or L != 2048 else config_lines(args, mw, wl, dev, stream, world)
+    sweep = None if args.no_configs or L != 2048 else accuracy_sweep(args, mw, wl, dev, acc)
+
+    # ---- rooflines per round trip: every stage against its own bound
     pk = peaks()
+    f64 = fp64_peak_live(dev)
+    if f64:
+        pk["fp64_tflops"], pk["fp64_src"] = f64, "torch.matmul float64 4096^3 (cuBLAS DGEMM), this run"
     pk_hbm = pk["hbm_gbs"]
     fb = fft_stage_bytes(L, B, args.precision)
     t = {k: v / 1e3 for k, v in stages.items()}  # seconds per round trip
@@ -454,7 +523,8 @@ def run_ours(args, rank, world, local_rank):
         stage_roof["delta"] = delta_roofline(recursion, L, t["delta"], pk, fp32_issue, n_sm, mhz)
     tc_flops = 2 * contraction_units(L, spins) * 4
     c_bytes = contraction_bytes(L, B, args.precision)
-    tc_peak = {"mixed": pk["bf16_tflops"], "mixed_tf32": pk["bf16_tflops"] * 0.5}.get(args.precision, 1.045)
+    tc_peak = {"mixed": pk["bf16_tflops"], "mixed_tf32": pk["bf16_tflops"] * 0.5}.get(args.precision,
+                                                                                       pk["fp64_tflops"])
     if t["contract"] > 0:
         a_t = tc_flops / t["contract"] / 1e12
         a_b = c_bytes / t["contract"] / 1e9
@@ -465,7 +535,7 @@ def run_ours(args, rank, world, local_rank):
                   "work": "4 flops per (l, m, m' >= 0, map) multiply-add, both directions",
                   "peak_src": {"mixed": "measured (MEASURED_PEAKS.json bf16 dense burst)",
                                "mixed_tf32": "measured BF16 peak x nominal TF32/BF16 ratio"}.get(
-                      args.precision, "measured (own FP64 mma.sync microbenchmark; same FP64 pipe as DFMA)")}
+                      args.precision, pk["fp64_src"])}
         hbm = {"achieved": a_b, "peak": pk_hbm, "unit": "GB/s", "frac": a_b / pk_hbm,
                "work": "staged planes read once per direction, G+ / N_l f_lm read, f_lm / F+ written",
                "peak_src": pk["src"]}
@@ -478,9 +548,7 @@ def run_ours(args, rank, world, local_rank):
             a = fb[k] / t[k] / 1e9
             stage_roof[k] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
                              "frac": a / pk["hbm_gbs"], "peak_src": pk["src"]}
-    # the Delta stage (recursion + contractions) against the largest of its
-    # floors: the recursion's own (FP64 flops for Risbo in double, FP32 issue or
-    # staging bytes otherwise), the tensor products, and the HBM bytes
+    # the Delta stage (recursion + contractions) against the largest of its floors
     t_d = t["delta"] + t["contract"]
     rec_floor = stage_roof["delta"]["floor_ms"] / 1e3 if "delta" in stage_roof else 0.0
     bounds = (rec_floor, tc_flops / (tc_peak * 1e12), c_bytes / (pk_hbm * 1e9))
@@ -494,52 +562,215 @@ def run_ours(args, rank, world, local_rank):
         rb_line["delta_roofline"] = delta_roofline("risbo_ff", L, rb_line["stage_ms_per_step"]["delta"] / 1e3, pk,
                                                    fp32_issue, n_sm, mhz)
     dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k])
-    if L == 2048 and B == 16 and args.precision == "mixed":
-        for k, v in TRAFFIC_L2048_B16.items():
-            if k == "delta" and recursion != "risbo_ff":
-                continue  # captured on the Risbo sweep
-            if k in stage_roof:
-                stage_roof[k]["traffic"] = sum(v) / len(v)  # bytes per launch, averaged over the launches
-                stage_roof[k]["traffic_per_step"] = sum(v) * (2 if k == "delta" else 1)
+    traffic = TRAFFIC.get((L, B, args.precision)) if recursion == "tn" else None
+    for k, v in (traffic or {}).items():
+        if k in stage_roof and v:
+            stage_roof[k]["traffic"] = sum(v) / len(v)  # DRAM bytes per launch, averaged over the launches
+            stage_roof[k]["traffic_per_step"] = sum(v)
     roof = dict(stage_roof[dom])
     roof["stage"] = dom
     roof.setdefault("traffic", None)
+    err = err_report["rel_max"]
+    meets = err <= 1e-6 and all(v["rel_max"] <= 1e-6 for v in acc.values())
     result = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms / K, "ms_per_step_median": statistics.median(each),
-        "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32+bf16", "mixed_tf32": "f64+f32+tf32"}[args.precision],
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f64+f32+bf16", "mixed_tf32": "f64+f32+tf32"}[args.precision],
         "data": "synthetic (seeded complex Gaussian f_lm, C_l=1/(l+1)^2)",
         "config": {"workload": f"MW round trip (inverse then forward) L={L}, B={B} (8 maps s=0, 8 maps s=2)",
-                   "L": L, "batch": B, "spins": spins, "precision": args.precision,
+                   "L": L, "batch": B, "precision": args.precision,
                    "l2_flush": "inputs larger than L2", "graph": True, "parallelism": f"replicas x{world}"},
-        "roundtrip_rel_err": err,
-        "roundtrip_errors": err_report,
-        "forward_rate": whole_job_value(world, B, K, fwd_ms / 1e3) / 2,
-        "inverse_rate": whole_job_value(world, B, K, inv_ms / 1e3) / 2,
-        "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
-                  "ms_per_step": fu_ms / K, "rel_err": fu_err,
-                  "what": "mw_forward_inverse: forward of B maps and inverse of B independent f_lm, one shared recursion"},
+        "gpu_launches": launches_per_step * K,
+        "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
+                "d2h_bytes_per_step": bytes_map + bytes_flm, "steps": K, "rel_err": e2e_err,
+                "ms_each_step": [round(x, 1) for x in e2e_each]},
+        "roofline": roof,
+        "clocks": ck,
+        "stage_roofline": stage_roof,
+        "delta_stage": delta_stage,
         "quadrature": {"value": world * B * K / (q_ms / 1e3), "unit": "integrals/s", "ms_per_call": q_ms / K,
                        "what": f"MW quadrature rule, {B} maps of L(L-1)+1 samples per call",
                        "roofline": {"bound": "hbm", "achieved": q_gbs, "peak": pk_hbm, "unit": "GB/s",
                                     "frac": q_gbs / pk_hbm, "kernel": "k_quad_partial"}},
         "real": {"value": whole_job_value(world, B, K, r_ms / 1e3), "unit": "transforms/s",
                  "ms_per_step": r_ms / K, "rel_err": r_err,
-                 "what": f"round trip of {B} real spin-0 maps (Sec. IV-G), uniform[-1,1] coefficients with the reality condition"},
+                 "what": f"round trip of {B} real spin-0 maps (Sec. IV-G), uniform[-1,1] coefficients"},
         "risbo": rb_line,
-        "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
-                "d2h_bytes_per_step": bytes_map + bytes_flm, "ms_each_step": e2e_each},
-        "gpu_launches": launches_per_step * K,
+        "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
+                  "ms_per_step": fu_ms / K, "rel_err": fu_err,
+                  "what": "mw_forward_inverse: forward of B maps and inverse of B independent f_lm, one recursion"},
+        "forward_rate": whole_job_value(world, B, K, fwd_ms / 1e3) / 2,
+        "inverse_rate": whole_job_value(world, B, K, inv_ms / 1e3) / 2,
+        "configs": configs,
+        "paper_accuracy_protocol": sweep,
         "stage_ms_per_step": stages,
-        "roofline": roof,
-        "stage_roofline": stage_roof,
-        "delta_stage": delta_stage,
-        "clocks": ck,
+        "ms_per_step_median": statistics.median(each),
+        "roundtrip_errors": err_report,
+        "mixed_vs_fp64_errors": acc or None,
+        "fp64_gpu": fp64_line,
+        "speedup_mixed_over_fp64": (value / fp64_line["value"]) if fp64_line else None,
+        "roundtrip_rel_err": err,
+        "meets_1e-6": meets,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(w, quick=False)
+        cb = cpu_baseline(w, quick=False)
+        result = {**{k: v for k, v in result.items() if k in HEAD_KEYS}, "cpu_baseline": cb,
+                  **{k: v for k, v in result.items() if k not in HEAD_KEYS}}
     return result
+
+
+HEAD_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+             "vs_baseline", "dtype", "data", "config", "gpu_launches", "e2e", "roofline", "clocks")
+
+
+def config_lines(args, mw, wl, dev, stream, world):
+    """The other workloads as secondary lines: FP64-path and mixed-path
+    transforms/s (graph-replayed round trips, or forward + adjoint for the
+    gradient workload) and errors against the FP64 oracle (on every map, or on
+    the maps named in `oracle_maps`) and of the mixed path against the FP64
+    path on every output."""
+    import numpy as np
+    import torch
+
+    import oracle
+    n_t = max(3, min(args.steps, 10))
+    out = {}
+
+    def rate(fn, n_transforms):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        ms, _ = timed_calls(fn, n_t, stream, dev)
+        return world * n_transforms * n_t / (ms / 1e3)
+
+    # configs 1 and 2: one map, FP64 inverse + forward against the oracle
+    for name, wk in (("c1_L32_s0", wl.workload_small()), ("c2_L256_s2", wl.workload_l256_s2())):
+        L, s = wk["L"], wk["spins"][0]
+        f = torch.from_numpy(np.stack(wk["flm"])).to(dev)
+        ref_map = oracle.inverse(wk["flm"][0], L, s)
+        line = {}
+        for prec in ("fp64", "mixed"):
+            p = mw.Plan(L, [s], precision=prec, graph=True)
+            m = torch.empty((1, mw.map_size(L)), dtype=torch.complex128, device=dev)
+            b = torch.empty_like(f)
+
+            def rt():
+                p.inverse(f, out=m)
+                p.forward(m, out=b)
+            r = rate(rt, 2)
+            mm = m.cpu().numpy()[0]
+            ref_back = oracle.forward(mm, L, s)
+            line[prec] = {"transforms_per_s": r,
+                          "inverse_vs_oracle": rel_np(mm, ref_map),
+                          "forward_vs_oracle": rel_np(b.cpu().numpy()[0], ref_back),
+                          "roundtrip_max_abs": float(np.max(np.abs(b.cpu().numpy()[0] - wk["flm"][0])))}
+            p.close()
+        out[name] = line
+
+    # config 3: 64 maps of uneven L and spin in one ragged plan, one graph launch per call
+    wk = wl.workload_ragged()
+    Ls, ss = wk["Ls"], wk["spins"]
+    f = torch.from_numpy(np.concatenate(wk["flm"])).to(dev)
+    line, maps_by = {}, {}
+    for prec in ("fp64", "mixed"):
+        p = mw.RaggedPlan(Ls, ss, precision=prec, graph=True)
+        m = torch.empty(p._nmap, dtype=torch.complex128, device=dev)
+        b = torch.empty_like(f)
+
+        def rt():
+            p.inverse(f, out=m)
+            p.forward(m, out=b)
+        line[prec] = {"transforms_per_s": rate(rt, 2 * len(Ls)),
+                      "roundtrip": rel_errors(b, f)}
+        maps_by[prec] = (m.clone(), p.map_offsets)
+        p.close()
+    line["mixed"]["inverse_vs_fp64"] = rel_errors(maps_by["mixed"][0], maps_by["fp64"][0])
+    seen, worst = set(), 0.0
+    mm, mo = maps_by["mixed"][0].cpu().numpy(), maps_by["mixed"][1]
+    for b, (L, s) in enumerate(zip(Ls, ss)):
+        if L in seen:
+            continue
+        seen.add(L)
+        worst = max(worst, rel_np(mm[mo[b]:mo[b] + mw.map_size(L)], oracle.inverse(wk["flm"][b], L, s))["rel_max"])
+    line["mixed"]["inverse_vs_oracle_rel_max"] = worst
+    line["oracle_maps"] = "one map of each band limit"
+    out["c3_ragged_64"] = line
+
+    # config 5: L = 512, 32 spin-0 maps of i.i.d. samples; the gradient step
+    # forward + forward adjoint (the backward of the loss)
+    wk = wl.workload_grad_l512_b32()
+    L = wk["L"]
+    x = torch.from_numpy(np.stack(wk["maps"])).to(dev)
+    tg = torch.from_numpy(np.stack(wk["targets"])).to(dev)
+    line, fwd_by = {}, {}
+    for prec in ("fp64", "mixed"):
+        p = mw.Plan(L, wk["spins"], precision=prec, graph=True)
+        y = torch.empty_like(tg)
+        gmap = torch.empty_like(x)
+
+        def step():
+            p.forward(x, out=y)
+            p.forward_adjoint(2 * (y - tg), out=gmap)
+        line[prec] = {"transforms_per_s": rate(step, 2 * len(wk["maps"]))}
+        p.forward(x, out=y)
+        fwd_by[prec] = y.clone()
+        p.close()
+    line["mixed"]["forward_vs_fp64"] = rel_errors(fwd_by["mixed"], fwd_by["fp64"])
+    ref = oracle.forward(wk["maps"][0], L, 0)
+    line["fp64"]["forward_vs_oracle"] = rel_np(fwd_by["fp64"][0].cpu().numpy(), ref)
+    line["mixed"]["forward_vs_oracle"] = rel_np(fwd_by["mixed"][0].cpu().numpy(), ref)
+    line["oracle_maps"] = "map 0"
+    out["c5_L512_B32_grad"] = line
+    return out
+
+
+def rel_np(x, ref):
+    import numpy as np
+    d = np.abs(np.asarray(x) - np.asarray(ref))
+    r = np.abs(np.asarray(ref))
+    return {"rel_max": float(d.max() / max(r.max(), 1e-300)),
+            "rel_rms": float(np.linalg.norm(d) / max(np.linalg.norm(r), 1e-300))}
+
+
+def accuracy_sweep(args, mw, wl, dev, acc):
+    """The paper's accuracy protocol (Sec. V-D): five signals per spin with Re,
+    Im uniform in [-1, 1], spins 0, 2 and 10, inverse then forward; the mean
+    over the five signals of the max-abs round-trip error per L, for the FP64
+    path and the mixed path.  At L = 2048 the mixed forward is also compared
+    with the FP64 forward per band of l (white coefficients put every band at
+    the same amplitude, so the per-band figures are not hidden by the global
+    normalisation)."""
+    import numpy as np
+    import torch
+    spins = [0] * 5 + [2] * 5 + [10] * 5
+    res = []
+    for L in (32, 64, 128, 256, 512, 1024, 2048):
+        g = wl.rng(7000 + L)
+        f = torch.from_numpy(np.stack([wl.uniform_flm(g, L, s) for s in spins])).to(dev)
+        row = {"L": L}
+        maps = {}
+        for prec in ("fp64", "mixed"):
+            p = mw.Plan(L, spins, precision=prec)
+            m = p.inverse(f)
+            b = p.forward(m)
+            e = (b - f).abs().amax(dim=1).cpu().numpy()
+            row[prec] = {str(s): float(np.mean(e[5 * k:5 * k + 5])) for k, s in enumerate((0, 2, 10))}
+            maps[prec] = (p, m)
+        if L == 2048:
+            p64, m64 = maps["fp64"]
+            fm = maps["mixed"][0].forward(m64)
+            f64 = p64.forward(m64)
+            rep = error_report(fm, f64, L)
+            acc["forward_vs_fp64_white"] = rep
+            acc["inverse_vs_fp64_white"] = rel_errors(maps["mixed"][1], m64)
+        for p, _ in maps.values():
+            p.close()
+        del maps
+        res.append(row)
+        torch.cuda.synchronize(dev)
+    return {"what": "mean over 5 signals of max|f_lm round trip - f_lm| (Re, Im uniform[-1,1]), by spin",
+            "rows": res}
 
 
 def cpu_baseline(w, quick=False):
@@ -588,6 +819,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tf32", "fp64"])
     ap.add_argument("--L", type=int, default=L_BENCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the FP64-path round trip")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads' lines and the paper's accuracy protocol")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -139,6 +139,31 @@ mw_status mw_plan_create_ragged(mw_plan **out, int n, const int *L, const int *s
 size_t mw_plan_map_elems(const mw_plan *plan);
 size_t mw_plan_flm_elems(const mw_plan *plan);
 
+/* Layout of a plan's buffers, as the plan computed it, so that callers need
+ * not re-derive it:
+ *   mw_plan_batch       number of maps b of the plan (real maps for a
+ *                       MW_FLAG_REAL plan, n for a ragged plan); 0 for NULL.
+ *   mw_plan_band_limit  L of map b (ragged plans: L[b]).
+ *   mw_plan_spin        spin of map b.
+ *   mw_plan_map_offset  element offset of map b in the map buffer (complex
+ *                       doubles; real doubles on a MW_FLAG_REAL plan): the
+ *                       prefix sum of (L-1)(2L-1)+1 over the maps before b.
+ *   mw_plan_flm_offset  element offset of map b's f_lm block (complex
+ *                       doubles): the prefix sum of L*L over the maps before b.
+ * For uniform plans these are b*N_MW and b*L*L.  Each returns -1 for a NULL
+ * plan or b outside [0, batch).  Host-only: no device work. */
+int mw_plan_batch(const mw_plan *plan);
+/* The same offsets without a plan (host-only, allocates nothing): for n maps of
+ * band limits L[0..n-1] (1 <= L[b] <= 2048), map_offsets[b] and flm_offsets[b]
+ * (either may be NULL) receive the prefix sums of (L-1)(2L-1)+1 and of L*L;
+ * entry n of each (arrays of n + 1 elements) receives the total.  MW_EINVAL for
+ * n < 1, a NULL L or a band limit out of range. */
+mw_status mw_layout_ragged(int n, const int *L, long long *map_offsets, long long *flm_offsets);
+int mw_plan_band_limit(const mw_plan *plan, int b);
+int mw_plan_spin(const mw_plan *plan, int b);
+long long mw_plan_map_offset(const mw_plan *plan, int b);
+long long mw_plan_flm_offset(const mw_plan *plan, int b);
+
 /* Forward transform (Sec. IV-D): map_in [batch][N_MW] -> flm_out [batch][L*L].
  * The result is that of the paper's algorithm: phi DFT of each ring (Eq. Gmt
  * discretised), periodic extension in theta with parity (-1)^(m+s), theta DFT
@@ -246,9 +271,12 @@ mw_status mw_plan_stage_times(mw_plan *plan, double *ms, long long *launches, in
  * pointers included, returns MW_EINVAL before anything is enqueued.
  * Scratch: the Wigner-Delta planes and the F_mm' coefficients live in one
  * static device array of MW_NOALLOC_SCRATCH_BYTES (about 2.6 MB), which every
- * GPU that loads libmw holds until the process exits.  The first call on a
- * device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture begins.
+ * GPU that loads libmw holds until the process exits.  Every call made
+ * outside a stream capture looks up that array's device address on the
+ * current device (so a context reset does not leave a stale address behind);
+ * a call made while its stream is being captured reuses the address the last
+ * such lookup on that device found, so make one call on each device before
+ * any stream capture begins.
  * Every call on a device uses the same array and finds the previous call's
  * contents there (the kernels clear what must start at zero), so calls whose
  * GPU work overlaps -- two streams, or two host threads -- race and give wrong

@@ -43,6 +43,10 @@ struct mw_plan {
   long long* d_moff = nullptr;
   long long* d_foff = nullptr;
   long long map_elems = 0, flm_elems = 0;  // totals over the plan's maps
+  // caller-facing layout, one entry per map of the caller's buffers (real maps
+  // of a real plan, every map of a ragged plan): band limit, spin, offsets
+  std::vector<int> q_L, q_s;
+  std::vector<long long> q_moff, q_foff;
   // ragged plans: one sub-plan per band limit; the parent owns the sweep state
   std::vector<mw_plan*> subs;
   bool shared_sweep = false;       // sweep state borrowed from a parent (not freed here)

@@ -153,6 +153,18 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     p->map_elems = (long long)nreal * nmw;
     p->flm_elems = (long long)nreal * L * L;
   }
+  {
+    const int nq = real ? nreal : B;
+    p->q_L.assign(nq, L);
+    p->q_s.resize(nq);
+    p->q_moff.resize(nq);
+    p->q_foff.resize(nq);
+    for (int b = 0; b < nq; ++b) {
+      p->q_s[b] = real ? 0 : spins[b];
+      p->q_moff[b] = real ? (long long)b * nmw : p->moff[b];
+      p->q_foff[b] = real ? (long long)b * L * L : p->foff[b];
+    }
+  }
   if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
 
   // spin groups (order of first appearance; at most kMaxGroupMaps maps each,
@@ -637,16 +649,15 @@ mw_status build_ragged(mw_plan** out, int n, const int* Ls, const int* spins, un
   *out = nullptr;
   if (n < 1 || n > (1 << 20) || !Ls || !spins || (flags & MW_FLAG_REAL)) return MW_EINVAL;
   int Lmax = 0;
-  std::vector<long long> moff(n), foff(n);
-  long long mo = 0, fo = 0;
   for (int b = 0; b < n; ++b) {
     if (Ls[b] < 1 || Ls[b] > 2048 || spins[b] <= -Ls[b] || spins[b] >= Ls[b]) return MW_EINVAL;
     Lmax = Ls[b] > Lmax ? Ls[b] : Lmax;
-    moff[b] = mo;
-    foff[b] = fo;
-    mo += (long long)(Ls[b] - 1) * (2 * Ls[b] - 1) + 1;
-    fo += (long long)Ls[b] * Ls[b];
   }
+  std::vector<long long> moff(n + 1), foff(n + 1);
+  if (mw_layout_ragged(n, Ls, moff.data(), foff.data()) != MW_OK) return MW_EINVAL;
+  const long long mo = moff[n], fo = foff[n];
+  moff.pop_back();
+  foff.pop_back();
   const int zero = 0;
   mw_plan* parent = nullptr;
   mw_status stt = build_plan(&parent, Lmax, 1, &zero, flags, nullptr, nullptr, nullptr, true);
@@ -655,6 +666,10 @@ mw_status build_ragged(mw_plan** out, int n, const int* Ls, const int* spins, un
   parent->spins.assign(spins, spins + n);
   parent->map_elems = mo;
   parent->flm_elems = fo;
+  parent->q_L.assign(Ls, Ls + n);
+  parent->q_s.assign(spins, spins + n);
+  parent->q_moff = moff;
+  parent->q_foff = foff;
   std::vector<int> done(n, 0);
   for (int b = 0; b < n; ++b) {
     if (done[b]) continue;
@@ -838,6 +853,28 @@ const char* mw_status_string(mw_status st) {
 
 size_t mw_plan_map_elems(const mw_plan* plan) { return plan ? (size_t)plan->map_elems : 0; }
 size_t mw_plan_flm_elems(const mw_plan* plan) { return plan ? (size_t)plan->flm_elems : 0; }
+
+mw_status mw_layout_ragged(int n, const int* L, long long* map_offsets, long long* flm_offsets) {
+  if (n < 1 || !L) return MW_EINVAL;
+  for (int b = 0; b < n; ++b)
+    if (L[b] < 1 || L[b] > 2048) return MW_EINVAL;
+  long long mo = 0, fo = 0;
+  for (int b = 0; b <= n; ++b) {
+    if (map_offsets) map_offsets[b] = mo;
+    if (flm_offsets) flm_offsets[b] = fo;
+    if (b == n) break;
+    mo += (long long)(L[b] - 1) * (2 * L[b] - 1) + 1;
+    fo += (long long)L[b] * L[b];
+  }
+  return MW_OK;
+}
+
+int mw_plan_batch(const mw_plan* plan) { return plan ? (int)plan->q_L.size() : 0; }
+static bool has_map(const mw_plan* plan, int b) { return plan && b >= 0 && b < (int)plan->q_L.size(); }
+int mw_plan_band_limit(const mw_plan* plan, int b) { return has_map(plan, b) ? plan->q_L[b] : -1; }
+int mw_plan_spin(const mw_plan* plan, int b) { return has_map(plan, b) ? plan->q_s[b] : -1; }
+long long mw_plan_map_offset(const mw_plan* plan, int b) { return has_map(plan, b) ? plan->q_moff[b] : -1; }
+long long mw_plan_flm_offset(const mw_plan* plan, int b) { return has_map(plan, b) ? plan->q_foff[b] : -1; }
 
 size_t mw_map_size(int L) { return L < 1 ? 0 : (size_t)(L - 1) * (2 * (size_t)L - 1) + 1; }
 size_t mw_flm_size(int L) { return L < 1 ? 0 : (size_t)L * (size_t)L; }

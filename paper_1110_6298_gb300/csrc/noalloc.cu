@@ -177,10 +177,13 @@ __global__ void __launch_bounds__(kSynthThreads) k_noalloc_synthesis(int L, cons
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device.
-mw_status scratch_address(int dev, double** out) {
+// Device address of g_scratch on the current device.  It is looked up again
+// on every call made outside a stream capture (a context reset or a reloaded
+// module may place the array elsewhere), and the last address seen is what a
+// call made during a capture uses.
+mw_status scratch_address(int dev, bool capturing, double** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!capturing || !g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
@@ -219,10 +222,15 @@ extern "C" mw_status mw_inverse_noalloc(int L, int s, const void* flm_in, void* 
   }
   if (dev < 0 || dev >= kMaxDevices) return MW_EUNSUPPORTED;
   if (!device_reachable(flm_in, dev) || !device_reachable(map_out, dev)) return MW_EINVAL;
-  double* scratch = nullptr;
-  const mw_status st = scratch_address(dev, &scratch);
-  if (st != MW_OK) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return MW_ECUDA;
+  }
+  double* scratch = nullptr;
+  const mw_status st = scratch_address(dev, cap != cudaStreamCaptureStatusNone, &scratch);
+  if (st != MW_OK) return st;
   k_noalloc_wigner<<<1, kWignerThreads, 0, cs>>>(L, s, static_cast<const double2*>(flm_in), scratch);
   k_noalloc_synthesis<<<L, kSynthThreads, 0, cs>>>(L, scratch, static_cast<double2*>(map_out));
   if (cudaGetLastError() != cudaSuccess) return MW_ECUDA;

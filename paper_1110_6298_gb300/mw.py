@@ -82,6 +82,17 @@ def lib():
         L.mw_forward_inverse.restype = c_int
         L.mw_inverse_noalloc.argtypes = [c_int, c_int, vp, vp, vp]
         L.mw_inverse_noalloc.restype = c_int
+        ll = ctypes.c_longlong
+        L.mw_plan_batch.argtypes = [vp]
+        L.mw_plan_batch.restype = c_int
+        for name in ("mw_plan_band_limit", "mw_plan_spin"):
+            getattr(L, name).argtypes = [vp, c_int]
+            getattr(L, name).restype = c_int
+        for name in ("mw_plan_map_offset", "mw_plan_flm_offset"):
+            getattr(L, name).argtypes = [vp, c_int]
+            getattr(L, name).restype = ll
+        L.mw_layout_ragged.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ll), ctypes.POINTER(ll)]
+        L.mw_layout_ragged.restype = c_int
         _lib = L
     return _lib
 
@@ -96,6 +107,19 @@ def map_size(L):
 
 def flm_size(L):
     return int(lib().mw_flm_size(int(L)))
+
+
+def layout_ragged(Ls):
+    """(map_offsets, flm_offsets), each of len(Ls) + 1 entries (the last is
+    the total), as the library lays out a ragged batch of band limits Ls."""
+    n = len(Ls)
+    la = (ctypes.c_int * n)(*[int(x) for x in Ls])
+    mo = (ctypes.c_longlong * (n + 1))()
+    fo = (ctypes.c_longlong * (n + 1))()
+    st = lib().mw_layout_ragged(n, la, mo, fo)
+    if st != MW_OK:
+        raise MWError(st, "mw_layout_ragged")
+    return list(mo), list(fo)
 
 
 def quadrature_size(L):
@@ -155,6 +179,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def layout(self):
+        """[(L, spin, map_offset, flm_offset)] per map, as the plan lays out
+        its buffers (read from the library)."""
+        h = self._h
+        n = int(lib().mw_plan_batch(h))
+        return [(int(lib().mw_plan_band_limit(h, b)), int(lib().mw_plan_spin(h, b)),
+                 int(lib().mw_plan_map_offset(h, b)), int(lib().mw_plan_flm_offset(h, b))) for b in range(n)]
 
     @property
     def workspace_bytes(self):
@@ -367,13 +399,9 @@ class RaggedPlan(Plan):
         self._h = h
         self._nmap = int(lib().mw_plan_map_elems(h))
         self._nflm = int(lib().mw_plan_flm_elems(h))
-        self.map_offsets, self.flm_offsets = [], []
-        mo = fo = 0
-        for L in Ls:
-            self.map_offsets.append(mo)
-            self.flm_offsets.append(fo)
-            mo += map_size(L)
-            fo += flm_size(L)
+        lay = self.layout()
+        self.map_offsets = [x[2] for x in lay]
+        self.flm_offsets = [x[3] for x in lay]
 
 
 NOALLOC_MAX_L = 128
@@ -389,8 +417,9 @@ def inverse_noalloc(L, s, flm, out):
     the caller provides both buffers.  flm: L*L complex128 on the current CUDA
     device; out: N_MW complex128 on that device.  L <= NOALLOC_MAX_L.  Calls
     share the static array, so calls whose GPU work overlaps (two streams or
-    threads) race; the first call on a device looks the array up and should
-    precede any stream capture.  Returns out.
+    threads) race; calls made outside a stream capture look the array's
+    address up, so one such call on each device should precede any stream
+    capture.  Returns out.
     """
     for name, t, n in (("flm", flm, flm_size(L)), ("out", out, map_size(L))):
         if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:

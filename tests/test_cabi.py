@@ -104,3 +104,35 @@ def test_flag_rules_checked_before_device_work(libmw):
     # an unknown flag bit
     assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, mixed | (1 << 12)) == c["MW_EINVAL"]
     assert not h.value
+
+
+def test_ragged_layout_prefix_sums(libmw):
+    """mw_layout_ragged: prefix sums of (L-1)(2L-1)+1 and L^2 in the caller's
+    order (Sec. IV-C sample count, Sec. III-B coefficient count), the total in
+    the last entry; bad band limits rejected; the per-plan queries answer -1 /
+    0 for a NULL plan."""
+    ll = ctypes.c_longlong
+    libmw.mw_layout_ragged.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ll),
+                                       ctypes.POINTER(ll)]
+    Ls = [64, 512, 1, 2, 384, 2048, 128]
+    n = len(Ls)
+    la = (ctypes.c_int * n)(*Ls)
+    mo, fo = (ll * (n + 1))(), (ll * (n + 1))()
+    assert libmw.mw_layout_ragged(n, la, mo, fo) == 0
+    em = ef = 0
+    for b, L in enumerate(Ls):
+        assert mo[b] == em and fo[b] == ef
+        em += (L - 1) * (2 * L - 1) + 1
+        ef += L * L
+    assert mo[n] == em and fo[n] == ef
+    assert libmw.mw_layout_ragged(n, la, None, fo) == 0
+    bad = (ctypes.c_int * 2)(8, 2049)
+    assert libmw.mw_layout_ragged(2, bad, mo, fo) == 1
+    assert libmw.mw_layout_ragged(0, la, mo, fo) == 1
+    for name in ("mw_plan_map_offset", "mw_plan_flm_offset"):
+        getattr(libmw, name).restype = ll
+        getattr(libmw, name).argtypes = [ctypes.c_void_p, ctypes.c_int]
+        assert getattr(libmw, name)(None, 0) == -1
+    libmw.mw_plan_band_limit.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert libmw.mw_plan_band_limit(None, 0) == -1
+    assert libmw.mw_plan_batch(None) == 0

@@ -150,12 +150,34 @@ def test_rejects_bad_arguments(mw):
         plan.forward(torch.zeros(5, dtype=torch.complex128, device="cuda"))
 
 
+# Sampled outputs of the full-size workload: 16 rings of the inverse (the
+# first and last few, the pole, and the interior), 16 m-columns of the forward
+# (|m| = 0, 1, 2, 3 and up to L-1 = 2047 on both signs).
+FULL_RINGS = [0, 1, 2, 255, 511, 767, 1023, 1279, 1535, 1791, 2000, 2043, 2044, 2045, 2046, 2047]
+FULL_MS = [-2047, -2046, -2045, -1500, -1000, -517, -3, -1, 0, 1, 2, 517, 1200, 1999, 2046, 2047]
+_ORACLE_CACHE = {}
+
+
+def _cached(key, fn):
+    """Oracle references of the full-size workload, computed once per module
+    (they do not depend on the GPU path's precision)."""
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = fn()
+    return _ORACLE_CACHE[key]
+
+
+def _full_size_maps(L, n):
+    """n i.i.d. complex Gaussian maps at L (the forward's full-size input)."""
+    return _cached(("maps", L, n), lambda: np.stack([wl.gaussian_map(wl.rng(4400 + b), L) for b in range(n)]))
+
+
 @pytest.mark.parametrize("prec", ["mixed", "mixed_tf32", "fp64"])
 def test_full_size_l2048_b16_sampled(mw, prec):
     """The benchmarked workload (L = 2048, 16 maps: 8 of spin 0, 8 of spin 2),
     in the benchmark's launch configuration, checked on sampled outputs: the
-    inverse on three rings (oracle ring synthesis), the forward of the GPU map
-    on eight m columns (oracle forward restricted to those m)."""
+    inverse on 16 rings including t = L-2 and the pole (oracle ring
+    synthesis), the forward of the GPU map on 16 m columns including
+    |m| = L-1 (oracle forward restricted to those m), and the round trip."""
     w = wl.workload_l2048_b16()
     L, spins = w["L"], w["spins"]
     flm = np.stack(w["flm"])
@@ -163,17 +185,21 @@ def test_full_size_l2048_b16_sampled(mw, prec):
     f_gpu = plan.inverse(torch.from_numpy(flm).cuda())
     back = plan.forward(f_gpu).cpu().numpy()
     f_np = f_gpu.cpu().numpy()
+    del f_gpu
+    x = _full_size_maps(L, len(spins))
+    fx = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     M = 2 * L - 1
-    rings = [0, 1023, L - 2]
-    ms = [-2047, -1000, -3, 0, 2, 517, 1999, 2047]
-    sel = np.isin(np.arange(L * L) - wl.ell_of_index(L) ** 2 - wl.ell_of_index(L), ms)
+    ell = wl.ell_of_index(L)
+    sel = np.isin(np.arange(L * L) - ell ** 2 - ell, FULL_MS)
     for s, idx in ((0, [0, 7]), (2, [8, 15])):
-        ref_r = oracle.inverse_rings(flm[idx], L, s, rings)
+        ref_r = _cached(("rings", s), lambda: oracle.inverse_rings(flm[idx], L, s, FULL_RINGS))
         for k, b in enumerate(idx):
-            got_r = np.stack([f_np[b][t * M:(t + 1) * M] for t in rings])
-            assert relmax(got_r, ref_r[k]) < TOL[prec]
-        ref_f = oracle.forward(f_np[idx], L, s, m_list=ms)
+            got_r = np.stack([f_np[b][t * M:(t + 1) * M] for t in FULL_RINGS[:-1]])
+            assert relmax(got_r, ref_r[k][:-1]) < TOL[prec]
+            # the pole ring is f(pi, 0) e^{i s phi}: its one stored sample is the phi = 0 entry
+            assert abs(f_np[b][(L - 1) * M] - ref_r[k][-1][0]) / np.max(np.abs(ref_r[k])) < TOL[prec]
+        ref_f = _cached(("fwd", s), lambda: oracle.forward(x[idx], L, s, m_list=FULL_MS))
         for k, b in enumerate(idx):
-            assert relmax(back[b][sel], ref_f[k][sel]) < TOL[prec]
+            assert relmax(fx[b][sel], ref_f[k][sel]) < TOL[prec]
             # band-limited input: the round trip is the identity
             assert np.max(np.abs(back[b] - flm[b])) / np.max(np.abs(flm[b])) < (1e-11 if prec == "fp64" else 1e-6)

@@ -115,3 +115,23 @@ def test_graph_replay_on_a_side_stream(mw):
     torch.cuda.synchronize()
     assert graphed.last_launches == 1
     assert torch.equal(out, ref)
+
+
+def test_plan_layout_queries(mw):
+    """The layout the C ABI reports for a plan (mw_plan_batch / band_limit /
+    spin / map_offset / flm_offset) equals the host-only mw_layout_ragged
+    prefix sums for a ragged plan, b * N_MW and b * L^2 for uniform and real
+    plans, and -1 past the last map."""
+    w = wl.workload_ragged()
+    Ls, spins = w["Ls"], w["spins"]
+    plan = mw.RaggedPlan(Ls, spins, precision="mixed")
+    mo, fo = mw.layout_ragged(Ls)
+    lay = plan.layout()
+    assert [x[0] for x in lay] == Ls and [x[1] for x in lay] == spins
+    assert [x[2] for x in lay] == mo[:-1] and [x[3] for x in lay] == fo[:-1]
+    assert mo[-1] == plan._nmap and fo[-1] == plan._nflm
+    assert mw.lib().mw_plan_map_offset(plan.handle, len(Ls)) == -1
+    up = mw.Plan(40, [0, 2, -1], precision="fp64")
+    assert up.layout() == [(40, s, b * mw.map_size(40), b * 1600) for b, s in enumerate([0, 2, -1])]
+    rp = mw.RealPlan(17, 3, precision="mixed")
+    assert rp.layout() == [(17, 0, b * mw.map_size(17), b * 289) for b in range(3)]
