@@ -1,5 +1,6 @@
 // internal.h -- plan layout and kernel entry points shared by the libmw sources.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -71,7 +72,16 @@ struct mw_plan {
   float2* d_tn_top = nullptr;      // MW_FLAG_DELTA_TN: top rows Delta^l_{l,m} as float-float mantissas
   int* d_tn_exp = nullptr;         // and their power-of-two exponents, plane l at l (l + 1) / 2
   double* d_nl = nullptr;          // sqrt((2l+1)/(4 pi)), l < L
-  float2* d_flmf = nullptr;        // mixed path: N_l f_lm in FP32 (input of the inverse contraction)
+  float2* d_flmf = nullptr;        // TF32x3 path: N_l f_lm in FP32 (input of the inverse contraction)
+  float2* d_flmT = nullptr;        // BF16x3 path: N_l f_lm in FP32 transposed to [B][M][L] (zero for l < |m|)
+  // BF16x3 contraction pipeline (kernels_tc2.cu): tensor maps of the staged
+  // planes (owner only), work items of this plan per (direction, chunk), and
+  // spin groups per pass (1 or 2)
+  CUtensorMap tmap_fwd{}, tmap_inv{};
+  bool tc2_maps = false;
+  int tc2_ng = 2;
+  int4* d_tc2_items = nullptr;
+  std::vector<int> tc2_off;
 
   // workspace
   void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
@@ -145,6 +155,13 @@ cudaError_t launch_phi_forward_real(const mw_plan* p, const double* maps, cudaSt
 cudaError_t launch_phi_inverse_real(const mw_plan* p, double* maps, cudaStream_t st);
 cudaError_t launch_real_unpack(const mw_plan* p, const double2* g, double2* flm, cudaStream_t st);
 cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, cudaStream_t st);
+// BF16x3 contraction pipeline: tensor maps of owner o's staging planes, the
+// work lists of plan p, the transposed N_l f_lm, and one chunk's contraction
+// (dir 0: Eq. flm_wig into flm; dir 1: Eq. Fmm into F+)
+cudaError_t make_tc2_tensor_maps(mw_plan* o);
+cudaError_t make_tc2_items(mw_plan* p);
+cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st);
+cudaError_t launch_tc2(const mw_plan* p, const mw_plan* o, int dir, int l0, int l1c, double2* flm, cudaStream_t st);
 // Trapani-Navaza planes l in [lb, le) into staging slots l - l0 (mixed paths)
 cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st);
 

@@ -491,7 +491,8 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     e = cudaMemsetAsync(q->d_Gp, 0, sizeof(double2) * (size_t)q->B * q->M * q->L, st);
     if (e != cudaSuccess) return e;
     if (!fp64) {
-      e = launch_flm_to_f32(q, jobs[c].flm_in, st);
+      e = (q->prec == MW_PREC_MIXED_BF16X3) ? launch_flm_transpose(q, jobs[c].flm_in, st)
+                                            : launch_flm_to_f32(q, jobs[c].flm_in, st);
       if (e != cudaSuccess) return e;
       ++nl;
     }
@@ -521,6 +522,8 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
       if (fp64)
         e = (jobs[c].mode == 0) ? launch_dmma_forward(q, l0, l1c, jobs[c].flm_out, st)
                                 : launch_dmma_inverse(q, l0, l1c, jobs[c].flm_in, st);
+      else if (q->prec == MW_PREC_MIXED_BF16X3)
+        e = launch_tc2(q, o, jobs[c].mode, l0, l1c, jobs[c].flm_out, st);
       else
         e = (jobs[c].mode == 0) ? launch_tc_forward(q, l0, l1c, jobs[c].flm_out, st)
                                 : launch_tc_inverse(q, l0, l1c, q->d_flmf, st);

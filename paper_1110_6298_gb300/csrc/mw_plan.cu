@@ -76,7 +76,7 @@ void free_plan(mw_plan* p) {
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
                   p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff,
-                  p->d_tn_top, p->d_tn_exp};
+                  p->d_tn_top, p->d_tn_exp, p->d_flmT, p->d_tc2_items};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -305,7 +305,8 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   if (!sweep_only) {
     alloc(&p->d_Gt, fsz * (size_t)B * M * L);
     alloc((void**)&p->d_Gp, sizeof(double2) * (size_t)B * M * L);
-    if (!dbl) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
+    if (prec == MW_PREC_MIXED_TF32X3) alloc((void**)&p->d_flmf, sizeof(float2) * (size_t)B * L * L);
+    if (prec == MW_PREC_MIXED_BF16X3) alloc((void**)&p->d_flmT, sizeof(float2) * (size_t)B * p->M * L);
     if (real) alloc((void**)&p->d_gpack, sizeof(double2) * (size_t)B * L * L);
   }
   if (owner) {  // borrow the parent's sweep state
@@ -358,12 +359,21 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
       alloc((void**)&p->d_tn_exp, sizeof(int) * nt);
       if (e == cudaSuccess) chk(cudaMemcpy(p->d_tn_exp, te.data(), sizeof(int) * nt, cudaMemcpyHostToDevice));
     }
+    if (e == cudaSuccess && prec == MW_PREC_MIXED_BF16X3) chk(make_tc2_tensor_maps(p));
     if (e == cudaSuccess) {
       int nsm = 0;
       chk(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
       p->risbo_grid = nsm * risbo_blocks_per_sm(p->prec);
       if (e == cudaSuccess) chk(make_risbo_perm(p));
     }
+  }
+  if (e == cudaSuccess && !sweep_only && prec == MW_PREC_MIXED_BF16X3) {
+    // spin groups per pass of the contraction pipeline: 2 (both groups of a
+    // plane tile in one pass) unless MW_TC2_GROUPS=1; results do not depend on it
+    if (const char* env = getenv("MW_TC2_GROUPS")) p->tc2_ng = (atoi(env) == 1) ? 1 : 2;
+    p->ws_bytes = ws;
+    chk(make_tc2_items(p));
+    ws = p->ws_bytes;
   }
   if (e != cudaSuccess) {
     const mw_status st = from_cuda(e);

@@ -14,8 +14,11 @@ therefore measure every band of l against its own largest reference value:
 * the benchmark's coefficients (C_l = 1/(l+1)^2): the FP32 stages leave an
   absolute error floor that does not depend on l, so each band's absolute
   error is held to 1e-6 of the batch's largest coefficient and the top
-  band's absolute error to at most BAND_GROWTH times the lowest band's
-  (an error growing with l breaks that).
+  band's absolute error to at most BAND_GROWTH times that of the band
+  above the lowest one (an error growing with l breaks that; the lowest band
+  is left out of the ratio because its largest coefficients, about 2000
+  times the top band's, carry the contraction's relative error on top of
+  the floor).
 
 The FP64 path these tests compare against is itself checked against the FP64
 oracle at 1e-12 on sampled rings and m-columns of the same size
@@ -112,4 +115,4 @@ def test_benchmark_coefficients_flat_error(mw):
               + "; (rel to band max): " + " ".join(f"{e / r:.2e}" for e, r in bands))
         for e, _ in bands:
             assert e / top < 1e-6
-        assert bands[-1][0] <= BAND_GROWTH * bands[0][0]
+        assert bands[-1][0] <= BAND_GROWTH * bands[1][0]

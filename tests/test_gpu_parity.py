@@ -166,9 +166,15 @@ def _cached(key, fn):
     return _ORACLE_CACHE[key]
 
 
-def _full_size_maps(L, n):
-    """n i.i.d. complex Gaussian maps at L (the forward's full-size input)."""
-    return _cached(("maps", L, n), lambda: np.stack([wl.gaussian_map(wl.rng(4400 + b), L) for b in range(n)]))
+def _full_size_maps(mw, flm, L, spins):
+    """The forward's full-size input: the FP64-path inverse of the workload's
+    coefficients (band-limited maps, the same for every precision tested)."""
+    def make():
+        p = mw.Plan(L, spins, precision="fp64")
+        x = p.inverse(torch.from_numpy(flm).cuda()).cpu().numpy()
+        p.close()
+        return x
+    return _cached(("maps64", L), make)
 
 
 @pytest.mark.parametrize("prec", ["mixed", "mixed_tf32", "fp64"])
@@ -186,7 +192,7 @@ def test_full_size_l2048_b16_sampled(mw, prec):
     back = plan.forward(f_gpu).cpu().numpy()
     f_np = f_gpu.cpu().numpy()
     del f_gpu
-    x = _full_size_maps(L, len(spins))
+    x = _full_size_maps(mw, flm, L, spins)
     fx = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     M = 2 * L - 1
     ell = wl.ell_of_index(L)
