@@ -13,30 +13,35 @@
 // tile in a fresh accumulator and the four correction products in a second
 // one, both summed across K tiles in float-float on the CUDA cores.
 //
-// What is new is the data flow.  Each CTA (one per SM) walks a list of work
-// items (am, row tile, spin-group slice); a work item is a run of 32-wide K
-// tiles, and the K tiles of all the CTA's items form one pipelined sequence:
-//   control warp   one thread loads the FP32 plane tiles of a K tile -- row am
-//                  and the spin rows |s| of the 128 (forward) or 32
-//                  (inverse) planes -- with plain per-CTA TMA
-//                  (cp.async.bulk.tensor, this GPU's memory only, no
-//                  multicast) two K tiles ahead, and issues the MMAs;
+// What is new is the data flow.  Each CTA (one per SM, 16 warps) walks a list
+// of work items (am, row tile, spin-group slice); a work item is a run of
+// 32-wide K tiles, and the K tiles of all the CTA's items form one pipelined
+// sequence:
 //   8 producer     form A for one row each (TMEM lane = row) for both spin
 //   warps          groups from one plane tile, split it, and store it straight
 //                  into tensor memory (tcgen05.st), so the MMAs read only B
 //                  from shared memory; they also split B into shared memory;
 //   8 drain warps  read the two accumulators per group (tcgen05.ld), add them
 //                  into float-float registers, release the accumulator, and
-//                  write the item's outputs after its last K tile.
+//                  write the item's outputs after its last K tile;
+//   control        one lane of the first drain warp loads the FP32 plane tiles
+//                  of a K tile -- row am and the spin rows |s| of the 128
+//                  (forward) or 32 (inverse) planes -- with plain per-CTA TMA
+//                  (cp.async.bulk.tensor, this GPU's memory only, no
+//                  multicast) four K tiles ahead, and issues the MMAs of the
+//                  next K tile before its warp drains the current one.
 // Operands and accumulators are double-buffered; stages are handed over with
-// mbarriers: TMA bytes -> producers -> MMA -> (producers, drain) -> MMA.  Every
-// wait is bounded: a wait that gives up records the timeout in the plan's error
-// word, raises the CTA's abort flag (which the other roles poll) and the CTA
-// leaves after the TMEM is released; the outputs of such a call are invalid.
+// mbarriers: TMA bytes -> producers -> MMA -> (producers, drain) -> MMA.  A
+// waiting thread is suspended in mbarrier.try_wait rather than spinning.
+// Every wait is bounded (2 s of wall clock): a wait that gives up records the
+// timeout in the plan's error word, raises the CTA's abort flag (which the
+// other roles poll) and the CTA leaves after its MMAs and TMA loads have
+// landed and the TMEM is released; the outputs of such a call are invalid.
 #include <cuda.h>
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -47,22 +52,24 @@ namespace {
 constexpr int kKT = 32;                    // K per tile (two K = 16 MMA steps)
 constexpr int kRows = 128;                 // rows of a tile (TMEM lanes)
 constexpr int kN = 32;                     // accumulator columns per spin group
-constexpr int kWarps = 17;                 // 1 control + 8 producer + 8 drain
+constexpr int kWarps = 16;                 // 8 producer + 8 drain (one drain lane also controls)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kTmaTile = 16384;            // one FP32 plane tile: 128 x 32 or 32 x 128 floats
 constexpr int kBTile = kN * kKT * 2;       // one BF16 split of B (2 KB)
 constexpr uint32_t kPolls = 1u << 24;
+constexpr uint32_t kWaitNs = 2000000000u;  // 2 s: a healthy wait ends within microseconds
 
 template <int NG>
 struct Layout {
+  static constexpr int kTS = NG == 2 ? 3 : 4;                        // TMA stages (plane tiles in flight)
   static constexpr int kTmaStage = (1 + NG) * kTmaTile;             // row am + one spin row per group
   static constexpr int kBStage = NG * 3 * kBTile;
   static constexpr int kTmaOff = 0;                                  // 1024-aligned
-  static constexpr int kBOff = 2 * kTmaStage;
-  static constexpr int kEpiOff = kBOff + 2 * kBStage;                // drain epilogue staging
-  static constexpr int kEpiBytes = 256 * NG * 32 * 4;                 // 256 drain threads x NG x 16 (hi, lo)
+  static constexpr int kBOff = kTS * kTmaStage;
+  static constexpr int kEpiOff = kBOff + 2 * kBStage;               // epilogue staging of one group
+  static constexpr int kEpiBytes = 32 * 256 * 4;                     // 32 values x 256 drain threads
   static constexpr int kBarOff = kEpiOff + kEpiBytes;
-  static constexpr int kBytes = kBarOff + 128;
+  static constexpr int kBytes = kBarOff + 192;
   static constexpr int kSmem = kBytes + 1024;                        // slack for the manual alignment
   // TMEM columns: accumulators (hi, corr) per buffer and group, then A per
   // stage, group, K step and split (8 columns = 16 bf16 of K each)
@@ -93,26 +100,42 @@ struct Tc2Args {
 };
 
 // ---- small PTX helpers --------------------------------------------------
+// One test of an mbarrier phase; a thread whose phase is not complete is
+// suspended (up to the hint, in ns) until it completes, so waiting warps do not
+// take issue slots from the working ones.
 __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(umma::smem_u32(bar)), "r"(parity)
+      : "r"(umma::smem_u32(bar)), "r"(parity), "r"(200000u)
       : "memory");
   return done != 0;
 }
+// Low 32 bits of the global nanosecond timer; differences are taken modulo
+// 2^32, which is exact for waits shorter than 4.29 s.
+__device__ __forceinline__ uint32_t now_ns() {
+  uint32_t t;
+  asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+  return t;
+}
 // Bounded wait that ignores the abort flag (the abort path's own waits).
 __device__ __forceinline__ bool wait_bar_all(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kPolls; ++it)
-    if (try_wait(bar, parity)) return true;
-  return false;
-}
-// Bounded wait that also gives up once another role has raised the abort flag.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t t0 = now_ns();
   for (uint32_t it = 0; it < kPolls; ++it) {
     if (try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && *abort_flag) return false;
+    if (now_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+// Bounded wait (kWaitNs of wall clock, at most kPolls tests) that also gives up
+// once another role has raised the abort flag.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (try_wait(bar, parity)) return true;
+  const uint32_t t0 = now_ns();
+  for (uint32_t it = 1; it < kPolls; ++it) {
+    if (try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0u && (*abort_flag || now_ns() - t0 > kWaitNs)) return false;
   }
   return false;
 }
@@ -197,22 +220,23 @@ __device__ __forceinline__ Item item_of(const Tc2Args& A, int it) {
 template <int DIR, int NG>
 __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUtensorMap tmap, Tc2Args A) {
   using Ly = Layout<NG>;
+  constexpr int kTS = Ly::kTS;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = umma::smem_u32(smem_raw);
   unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Ly::kBarOff);
-  uint64_t* tma_full = bar;      // [2] TMA bytes of a stage arrived
-  uint64_t* full = bar + 2;      // [2] producers wrote A (TMEM) and B (smem) of a stage
-  uint64_t* done = bar + 4;      // [2] the MMAs of a stage completed
-  uint64_t* accempty = bar + 6;  // [2] the drain read an accumulator buffer
-  uint64_t* fin = bar + 8;       // final MMA completion on the abort path
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 9);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 10);
+  uint64_t* tma_full = bar;             // [kTS] TMA bytes of a plane-tile stage arrived
+  uint64_t* full = bar + kTS;           // [2] producers wrote A (TMEM) and B (smem) of an operand stage
+  uint64_t* done = bar + kTS + 2;       // [2] the MMAs of an operand stage completed
+  uint64_t* accempty = bar + kTS + 4;   // [2] the drain read an accumulator buffer
+  uint64_t* fin = bar + kTS + 6;        // final MMA completion on the abort path
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kTS + 7);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + kTS + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   if (tid == 0) {
+    for (int t = 0; t < kTS; ++t) umma::mbar_init(&tma_full[t], 1);
     for (int s = 0; s < 2; ++s) {
-      umma::mbar_init(&tma_full[s], 1);
       umma::mbar_init(&full[s], 8);
       umma::mbar_init(&done[s], 1);
       umma::mbar_init(&accempty[s], 8);
@@ -233,226 +257,290 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     atomicOr(A.err, 1);
   };
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ control
-    if (lane == 0) {
-      const uint32_t idesc = umma::idesc_bf16_f32(kRows, kN);
-      // TMA of sequence position (it, kt) into stage s
-      auto issue_tma = [&](int it, int kt, int s) {
-        const Item x = item_of<DIR>(A, it);
-        const int ngl = min(NG, A.ng - x.gs * NG);
-        arrive_expect_tx(&tma_full[s], (uint32_t)((1 + NG) * kTmaTile));
-        const uint32_t dst = tma_base + (uint32_t)(s * Ly::kTmaStage);
-        int xx, zz;
-        if (DIR == 0) { xx = kKT * kt; zz = x.t0 - A.l0; }               // 32 m' of 128 planes
-        else { xx = x.t0; zz = x.kstart + kKT * kt - A.l0; }             // 128 m' of 32 planes
-        tma_load_3d(dst, &tmap, xx, x.am, zz, &tma_full[s]);
-        for (int g = 0; g < NG; ++g) {
-          // a slice with fewer groups loads its last spin row again (bytes must match)
-          const int s_g = A.groups[x.gs * NG + min(g, ngl - 1)].s;
-          tma_load_3d(dst + (uint32_t)((1 + g) * kTmaTile), &tmap, xx, s_g < 0 ? -s_g : s_g, zz, &tma_full[s]);
-        }
-      };
-      // the sequence: items blockIdx.x, +G, ...; K tiles of each
-      int it_n = blockIdx.x, kt_n = 0;  // position two ahead (TMA prefetch)
-      int n_tma[2] = {0, 0};            // TMA loads issued per stage
-      auto advance = [&](int& it, int& kt) {
-        if (++kt >= A.items[it].w) { kt = 0; it += G; }
-      };
-      for (int s = 0; s < 2 && it_n < A.nitems; ++s) {
-        issue_tma(it_n, kt_n, s);
-        ++n_tma[s];
-        advance(it_n, kt_n);
-      }
-      int q = 0;
-      bool ok = true;
-      for (int it = blockIdx.x; ok && it < A.nitems; it += G) {
-        const Item x = item_of<DIR>(A, it);
-        const int ngl = min(NG, A.ng - x.gs * NG);
-        for (int kt = 0; kt < x.nk; ++kt, ++q) {
-          const int s = q & 1;
-          const uint32_t ph = (uint32_t)(q >> 1) & 1u;
-          if (!wait_bar(&full[s], ph, abort_flag)) { fail(); ok = false; break; }
-          if (q >= 2 && !wait_bar(&accempty[s], ph ^ 1u, abort_flag)) { fail(); ok = false; break; }
-          umma::fence_after();
-          for (int g = 0; g < ngl; ++g) {
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-#pragma unroll
-              for (int p = 0; p < 6; ++p) {
-                const uint32_t bd_addr = b_base + (uint32_t)(s * Ly::kBStage + (g * 3 + split_b(p)) * kBTile + ks * 256);
-                const uint64_t bd = umma::smem_desc(bd_addr, 128, (kKT / 8) * 128);
-                const uint32_t d = tmem + (p == 0 ? Ly::acc_hi(s, g) : Ly::acc_corr(s, g));
-                const int acc = (p == 0) ? (ks > 0) : !(ks == 0 && p == 1);
-                mma_ta(d, tmem + Ly::a_col(s, g, ks, split_a(p)), bd, idesc, acc);
-              }
-            }
-          }
-          umma::commit(&done[s]);
-          if (it_n < A.nitems) {  // the TMA tiles of stage s were read: refill two ahead
-            issue_tma(it_n, kt_n, s);
-            ++n_tma[s];
-            advance(it_n, kt_n);
-          }
-        }
-      }
-      if (!ok) {
-        // let the MMAs already issued finish before the TMEM is released, and
-        // the TMA loads already issued land before the CTA's shared memory goes
-        umma::commit(fin);
-        wait_bar_all(fin, 0);
-        for (int s = 0; s < 2; ++s)
-          if (n_tma[s] > 0) wait_bar_all(&tma_full[s], (uint32_t)(n_tma[s] - 1) & 1u);
-      }
-    }
-    __syncwarp();
-  } else if (warp <= 8) {
+  if (warp < 8) {
     // ----------------------------------------------------------- producers
-    const int pw = warp - 1, ks = pw >> 2, qd = warp & 3;
+    const int ks = warp >> 2, qd = warp & 3;
     const int r = 32 * qd + lane;                       // tile row = TMEM lane
     const uint32_t lane_addr = (uint32_t)(32 * qd) << 16;
-    const int pt = pw * 32 + lane;                      // B unit: group pt / 128, row n, 8-wide K chunk
+    const int pt = warp * 32 + lane;                    // B unit: group pt / 128, row n, 8-wide K chunk
     const int bg = pt >> 7, bn = (pt >> 2) & 31, bkc = pt & 3;
-    float bcur[8], bnext[8];
-    // B values of sequence position (it, kt): 8 consecutive K of row bn of group bg
-    auto load_b = [&](int it, int kt, float* v) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    // B cursor, two positions ahead of the A position: 8 consecutive K of row
+    // bn of group bg; the item's row pointer and signs are decoded once per item
+    struct BPos {
+      int it, kt, nk, k0;
+      const float2* row;
+      bool valid, neg;
+    } P;
+    const int kend = DIR == 0 ? A.L : A.l1c;
+    auto load_bpos = [&](int it) {
+      P.it = it;
+      P.kt = 0;
+      P.valid = false;
       if (it >= A.nitems) return;
       const Item x = item_of<DIR>(A, it);
+      P.nk = x.nk;
+      P.k0 = x.kstart + 8 * bkc;  // m' (forward) or l (inverse)
       const int gidx = x.gs * NG + bg;
       if (bg >= NG || gidx >= A.ng) return;
       const SpinGroup& g = A.groups[gidx];
       const int j = bn >> 1, nb = g.nb;
       if (j >= 2 * nb) return;
-      const bool neg = j >= nb;
-      if (neg && x.am == 0) return;
-      const int map = g.maps[neg ? j - nb : j];
-      const int k0 = x.kstart + kKT * kt + 8 * bkc;  // m' (forward) or l (inverse)
-      const float2* row = A.bsrc + ((size_t)map * A.M + (neg ? -x.am : x.am) + A.L - 1) * A.L;
-      const int kend = DIR == 0 ? A.L : A.l1c;
+      P.neg = j >= nb;
+      if (P.neg && x.am == 0) return;
+      const int map = g.maps[P.neg ? j - nb : j];
+      P.row = A.bsrc + ((size_t)map * A.M + (P.neg ? -x.am : x.am) + A.L - 1) * A.L;
+      P.valid = true;
+    };
+    // The loads only: each value is the re or im word of a G+ / N_l f_lm
+    // entry, read straight into the buffer (a predicated load leaves 0 past
+    // the end), and the (-1)^k of the -am fold is recorded as a sign mask, so
+    // no instruction waits for the data until the buffer is stored two
+    // positions later.
+    auto load_b = [&](float (&v)[8], uint32_t& sgn) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int k = k0 + i;
-        if (k < kend) {
-          const float2 f = __ldg(row + k);
-          float y = (bn & 1) ? f.y : f.x;
-          if (neg && (k & 1)) y = -y;  // (-1)^m' (forward) or (-1)^l (inverse) of the -am fold
-          v[i] = y;
-        }
+      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      sgn = 0u;
+      if (P.it >= A.nitems) return;
+      if (P.valid) {
+        const int k0 = P.k0 + kKT * P.kt;
+        const float* src = reinterpret_cast<const float*>(P.row + k0) + (bn & 1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (k0 + i < kend) v[i] = __ldg(src + 2 * i);
+        // (-1)^m' (forward) or (-1)^l (inverse) of the -am fold: odd k negated
+        if (P.neg) sgn = (k0 & 1) ? 0x55u : 0xAAu;  // bit i set: entry k0 + i is odd
       }
+      if (++P.kt >= P.nk) load_bpos(P.it + G);
     };
-    int it_b = blockIdx.x, kt_b = 0;  // position of bnext
-    auto adv = [&](int& it, int& kt) {
-      if (++kt >= A.items[it].w) { kt = 0; it += G; }
+    // the A position (item, K tile) and the item's spins
+    int it = blockIdx.x, kt = 0, q = 0;
+    Item x{};
+    int ngl = 0, spin[NG];
+    auto load_item = [&]() {
+      if (it >= A.nitems) return;
+      x = item_of<DIR>(A, it);
+      ngl = min(NG, A.ng - x.gs * NG);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) spin[g] = g < ngl ? A.groups[x.gs * NG + g].s : 0;
     };
-    if (it_b < A.nitems) {
-      load_b(it_b, kt_b, bcur);
-      adv(it_b, kt_b);
-    }
-    int q = 0;
-    bool ok = true;
-    for (int it = blockIdx.x; ok && it < A.nitems; it += G) {
-      const Item x = item_of<DIR>(A, it);
-      const int ngl = min(NG, A.ng - x.gs * NG);
-      for (int kt = 0; kt < x.nk; ++kt, ++q) {
-        const int s = q & 1;
-        const uint32_t ph = (uint32_t)(q >> 1) & 1u;
-        load_b(it_b, kt_b, bnext);  // next position's B, in flight during this one
-        // every lane waits; the outcome is made warp-uniform so that the
-        // warp-collective TMEM stores and __syncwarp below never diverge
-        bool w = (q < 2 || wait_bar(&done[s], ph ^ 1u, abort_flag)) && wait_bar(&tma_full[s], ph, abort_flag);
-        if (!__all_sync(0xffffffffu, w)) { if (lane == 0) fail(); ok = false; break; }
-        umma::fence_after();
-        const float* T = reinterpret_cast<const float*>(smem + Ly::kTmaOff + s * Ly::kTmaStage);
-        // row am of the planes (shared by the groups)
-        float a[16];
-        if (DIR == 0) {
-          // forward: tile [128 planes][32 m'] with the 128-byte swizzle (16-byte
-          // chunk c of row r stored at chunk c ^ (r & 7))
+    load_item();
+    float b0[8], b1[8];
+    uint32_t sg0, sg1;
+    load_bpos(blockIdx.x);
+    load_b(b0, sg0);
+    load_b(b1, sg1);
+    // One position: B of this position (loaded two positions ago) into
+    // operand stage s, the B loads of the position two ahead, then A from the
+    // plane tiles of TMA stage q % kTS into tensor memory.
+    auto body = [&](float (&cur)[8], uint32_t& csg) -> bool {
+      if (it >= A.nitems) return false;
+      const int s = q & 1, ts = q % kTS;
+      const uint32_t ph = (uint32_t)(q >> 1) & 1u, tph = (uint32_t)(q / kTS) & 1u;
+      // every lane waits; the outcome is made warp-uniform so that the
+      // warp-collective TMEM stores and __syncwarp below never diverge
+      const bool w = (q < 2 || wait_bar(&done[s], ph ^ 1u, abort_flag)) && wait_bar(&tma_full[ts], tph, abort_flag);
+      if (!__all_sync(0xffffffffu, w)) {
+        if (lane == 0) fail();
+        return false;
+      }
+      umma::fence_after();
+      if (bg < NG) {
+        uint32_t h[4], m[4], l[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float4 v = *reinterpret_cast<const float4*>(T + r * 32 + (((4 * ks + c) ^ (r & 7)) << 2));
-            a[4 * c] = v.x; a[4 * c + 1] = v.y; a[4 * c + 2] = v.z; a[4 * c + 3] = v.w;
-          }
-        } else {
-          // inverse: tile [32 planes][128 m'], row-major
+        for (int i = 0; i < 8; ++i) cur[i] = __uint_as_float(__float_as_uint(cur[i]) ^ (((csg >> i) & 1u) << 31));
 #pragma unroll
-          for (int i = 0; i < 16; ++i) a[i] = T[(16 * ks + i) * 128 + r];
+        for (int i = 0; i < 4; ++i) split_pair(cur[2 * i], cur[2 * i + 1], h[i], m[i], l[i]);
+        unsigned char* sb = smem + Ly::kBOff + s * Ly::kBStage + bg * 3 * kBTile;
+        const int off = umma::tile_off(bn, 8 * bkc, kKT / 8);
+        *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(sb + kBTile + off) = make_uint4(m[0], m[1], m[2], m[3]);
+        *reinterpret_cast<uint4*>(sb + 2 * kBTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+      load_b(cur, csg);
+      const float* T = reinterpret_cast<const float*>(smem + Ly::kTmaOff + ts * Ly::kTmaStage);
+      // row am of the planes (shared by the groups)
+      float a[16];
+      if (DIR == 0) {
+        // forward: tile [128 planes][32 m'] with the 128-byte swizzle (16-byte
+        // chunk c of row r stored at chunk c ^ (r & 7))
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(T + r * 32 + (((4 * ks + c) ^ (r & 7)) << 2));
+          a[4 * c] = v.x; a[4 * c + 1] = v.y; a[4 * c + 2] = v.z; a[4 * c + 3] = v.w;
         }
+      } else {
+        // inverse: tile [32 planes][128 m'], row-major
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          const float* W = T + (1 + g) * (kTmaTile / 4);
-          uint32_t hp[8], mp[8], lp[8];
-          if (g < ngl) {
-            const SpinGroup& sg = A.groups[x.gs * NG + g];
-            const int sv = sg.s, as = sv < 0 ? -sv : sv;
-            if (DIR == 0) {
-              const int l = x.t0 + r, mp0 = kKT * kt + 16 * ks;
-              const bool row_ok = l >= x.am && l < A.l1c && l >= as;
-              // sign (-1)^(am + as) (-1)^(l + m') [s > 0]; m' parity alternates along the row
-              const float s0 = (((x.am + as + (sv > 0 ? l + mp0 : 0)) & 1) ? -1.f : 1.f);
-              const float s1 = sv > 0 ? -s0 : s0;
-              const int lim = row_ok ? l - mp0 : -1;  // entries i <= lim are inside the plane
+        for (int i = 0; i < 16; ++i) a[i] = T[(16 * ks + i) * 128 + r];
+      }
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const float4 v = *reinterpret_cast<const float4*>(W + r * 32 + (((4 * ks + c) ^ (r & 7)) << 2));
-                float x0 = a[4 * c] * v.x * s0, x1 = a[4 * c + 1] * v.y * s1;
-                float x2 = a[4 * c + 2] * v.z * s0, x3 = a[4 * c + 3] * v.w * s1;
+      for (int g = 0; g < NG; ++g) {
+        const float* W = T + (1 + g) * (kTmaTile / 4);
+        uint32_t hp[8], mp[8], lp[8];
+        if (g < ngl) {
+          const int sv = spin[g], as = sv < 0 ? -sv : sv;
+          if (DIR == 0) {
+            const int l = x.t0 + r, mp0 = kKT * kt + 16 * ks;
+            const bool row_ok = l >= x.am && l < A.l1c && l >= as;
+            // sign (-1)^(am + as) (-1)^(l + m') [s > 0]; m' parity alternates along the row
+            const float s0 = (((x.am + as + (sv > 0 ? l + mp0 : 0)) & 1) ? -1.f : 1.f);
+            const float s1 = sv > 0 ? -s0 : s0;
+            const int lim = row_ok ? l - mp0 : -1;  // entries i <= lim are inside the plane
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float4 v = *reinterpret_cast<const float4*>(W + r * 32 + (((4 * ks + c) ^ (r & 7)) << 2));
+              float x0 = a[4 * c] * v.x * s0, x1 = a[4 * c + 1] * v.y * s1;
+              float x2 = a[4 * c + 2] * v.z * s0, x3 = a[4 * c + 3] * v.w * s1;
+              if (lim < 15) {  // the K step crosses the edge of the plane
                 if (4 * c > lim) x0 = 0.f;
                 if (4 * c + 1 > lim) x1 = 0.f;
                 if (4 * c + 2 > lim) x2 = 0.f;
                 if (4 * c + 3 > lim) x3 = 0.f;
-                split_pair(x0, x1, hp[2 * c], mp[2 * c], lp[2 * c]);
-                split_pair(x2, x3, hp[2 * c + 1], mp[2 * c + 1], lp[2 * c + 1]);
               }
-            } else {
-              const int mpr = x.t0 + r, lb = x.kstart + kKT * kt + 16 * ks;
-              const float s0 = (((x.am + as + (sv > 0 ? lb + mpr : 0)) & 1) ? -1.f : 1.f);
-              const float s1 = sv > 0 ? -s0 : s0;
-              const int lo_i = max(max(mpr, as) - lb, 0), hi_i = A.l1c - lb;  // valid i in [lo_i, hi_i)
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                float x0 = a[2 * i] * W[(16 * ks + 2 * i) * 128 + r] * s0;
-                float x1 = a[2 * i + 1] * W[(16 * ks + 2 * i + 1) * 128 + r] * s1;
-                if (2 * i < lo_i || 2 * i >= hi_i) x0 = 0.f;
-                if (2 * i + 1 < lo_i || 2 * i + 1 >= hi_i) x1 = 0.f;
-                split_pair(x0, x1, hp[i], mp[i], lp[i]);
-              }
+              split_pair(x0, x1, hp[2 * c], mp[2 * c], lp[2 * c]);
+              split_pair(x2, x3, hp[2 * c + 1], mp[2 * c + 1], lp[2 * c + 1]);
             }
           } else {
+            const int mpr = x.t0 + r, lb = x.kstart + kKT * kt + 16 * ks;
+            const float s0 = (((x.am + as + (sv > 0 ? lb + mpr : 0)) & 1) ? -1.f : 1.f);
+            const float s1 = sv > 0 ? -s0 : s0;
+            const int lo_i = max(max(mpr, as) - lb, 0), hi_i = A.l1c - lb;  // valid i in [lo_i, hi_i)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) hp[i] = mp[i] = lp[i] = 0u;
+            for (int i = 0; i < 8; ++i) {
+              float x0 = a[2 * i] * W[(16 * ks + 2 * i) * 128 + r] * s0;
+              float x1 = a[2 * i + 1] * W[(16 * ks + 2 * i + 1) * 128 + r] * s1;
+              if (lo_i > 0 || hi_i < 16) {  // the K step crosses an edge
+                if (2 * i < lo_i || 2 * i >= hi_i) x0 = 0.f;
+                if (2 * i + 1 < lo_i || 2 * i + 1 >= hi_i) x1 = 0.f;
+              }
+              split_pair(x0, x1, hp[i], mp[i], lp[i]);
+            }
           }
-          tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 0), hp);
-          tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 1), mp);
-          tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 2), lp);
-        }
-        // B: 8 K of row bn of group bg, split into the K-major core-matrix layout
-        if (bg < NG) {
-          uint32_t h[4], m[4], l[4];
+        } else {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) split_pair(bcur[2 * i], bcur[2 * i + 1], h[i], m[i], l[i]);
-          unsigned char* sb = smem + Ly::kBOff + s * Ly::kBStage + bg * 3 * kBTile;
-          const int off = umma::tile_off(bn, 8 * bkc, kKT / 8);
-          *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(sb + kBTile + off) = make_uint4(m[0], m[1], m[2], m[3]);
-          *reinterpret_cast<uint4*>(sb + 2 * kBTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          for (int i = 0; i < 8; ++i) hp[i] = mp[i] = lp[i] = 0u;
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) bcur[i] = bnext[i];
-        if (it_b < A.nitems) adv(it_b, kt_b);
-        tmem_wait_st();
-        umma::fence_proxy_async();
-        umma::fence_before();
-        __syncwarp();
-        if (lane == 0) arrive(&full[s]);
+        tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 0), hp);
+        tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 1), mp);
+        tmem_st8(tmem + lane_addr + Ly::a_col(s, g, ks, 2), lp);
       }
+      tmem_wait_st();
+      umma::fence_proxy_async();
+      umma::fence_before();
+      __syncwarp();
+      if (lane == 0) arrive(&full[s]);
+      ++q;
+      if (++kt >= x.nk) {
+        kt = 0;
+        it += G;
+        load_item();
+      }
+      return true;
+    };
+    // two copies of the body, so that the B buffers alternate without moves
+    while (body(b0, sg0) && body(b1, sg1)) {
     }
   } else {
     // --------------------------------------------------------------- drain
-    const int dw = warp - 9, half = dw >> 2, qd = warp & 3;
+    // Warps 8..15; lane 0 of warp 8 is also the control thread: it loads the
+    // FP32 plane tiles by TMA kTS positions ahead and issues the MMAs of the
+    // next position before its warp drains the current one, so the tensor
+    // core works on position q+1 while the drain warps read position q.
+    const int dw = warp - 8, half = dw >> 2, qd = warp & 3;
     const uint32_t lane_addr = (uint32_t)(32 * qd) << 16;
+    const bool ctl = warp == 8 && lane == 0;
+    struct TmaPos {
+      int it, kt, nk, am, t0, kstart;
+      int asr[NG];
+    } P;  // TMA cursor (kTS positions ahead of the MMA cursor)
+    struct MmaPos {
+      int it, kt, nk, ngl;
+    } Qm;  // MMA cursor
+    int n_tma = 0;  // TMA loads issued (stage t took those with index % kTS == t)
+    int qm = 0;  // MMA position
+    bool cok = true;
+    auto load_pos = [&](int itp) {
+      P.it = itp;
+      P.kt = 0;
+      if (itp >= A.nitems) return;
+      const Item y = item_of<DIR>(A, itp);
+      P.nk = y.nk; P.am = y.am; P.t0 = y.t0; P.kstart = y.kstart;
+      const int ngl = min(NG, A.ng - y.gs * NG);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        // a slice with fewer groups loads its last spin row again (bytes must match)
+        const int sg = A.groups[y.gs * NG + min(g, ngl - 1)].s;
+        P.asr[g] = sg < 0 ? -sg : sg;
+      }
+    };
+    auto issue_tma = [&](int t) {
+      arrive_expect_tx(&tma_full[t], (uint32_t)((1 + NG) * kTmaTile));
+      const uint32_t dst = tma_base + (uint32_t)(t * Ly::kTmaStage);
+      int xx, zz;
+      if (DIR == 0) { xx = kKT * P.kt; zz = P.t0 - A.l0; }               // 32 m' of 128 planes
+      else { xx = P.t0; zz = P.kstart + kKT * P.kt - A.l0; }             // 128 m' of 32 planes
+      tma_load_3d(dst, &tmap, xx, P.am, zz, &tma_full[t]);
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        tma_load_3d(dst + (uint32_t)((1 + g) * kTmaTile), &tmap, xx, P.asr[g], zz, &tma_full[t]);
+      ++n_tma;
+      if (++P.kt >= P.nk) load_pos(P.it + G);
+    };
+    auto load_mpos = [&](int itp) {
+      Qm.it = itp;
+      Qm.kt = 0;
+      if (itp >= A.nitems) return;
+      const int4 v = A.items[itp];
+      Qm.nk = v.w;
+      Qm.ngl = min(NG, A.ng - v.z * NG);
+    };
+    const uint32_t idesc = umma::idesc_bf16_f32(kRows, kN);
+    const uint64_t bdesc0 = umma::smem_desc(b_base, 128, (kKT / 8) * 128);
+    // MMAs of the MMA cursor's position, then the TMA kTS positions ahead
+    auto mma_step = [&]() {
+      if (!cok || Qm.it >= A.nitems) return;
+      const int st = qm & 1;
+      const uint32_t ph = (uint32_t)(qm >> 1) & 1u;
+      if (!wait_bar(&full[st], ph, abort_flag) || (qm >= 2 && !wait_bar(&accempty[st], ph ^ 1u, abort_flag))) {
+        fail();
+        cok = false;
+        return;
+      }
+      umma::fence_after();
+      // descriptor start-address fields advance by offset / 16 (no carry below
+      // 256 KB); TMEM addresses are constant offsets from the stage's bases.
+      // Consecutive MMAs go to different accumulators (the groups' hi and
+      // correction slots), so that accumulation chains overlap in the pipe.
+      const uint64_t bd_s = bdesc0 + (uint64_t)((st * Ly::kBStage) >> 4);
+      const uint32_t acc_s = tmem + Ly::acc_hi(st, 0), a_s = tmem + Ly::a_col(st, 0, 0, 0);
+      auto issue = [&](auto ngc) {
+        constexpr int NGC = decltype(ngc)::value;
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2)
+#pragma unroll
+          for (int p = 0; p < 6; ++p)
+#pragma unroll
+            for (int g = 0; g < NGC; ++g)
+              mma_ta(acc_s + (uint32_t)(g * 64 + (p == 0 ? 0 : 32)),
+                     a_s + (uint32_t)((g * 2 + k2) * 24 + split_a(p) * 8),
+                     bd_s + (uint64_t)((((g * 3 + split_b(p)) * kBTile) + k2 * 256) >> 4), idesc,
+                     (p == 0) ? (k2 > 0) : !(k2 == 0 && p == 1));
+      };
+      if (NG == 2 && Qm.ngl == 2) issue(std::integral_constant<int, NG>{});
+      else issue(std::integral_constant<int, 1>{});
+      umma::commit(&done[st]);
+      // the plane tiles of this position were read (full was observed): refill
+      if (P.it < A.nitems) issue_tma(qm % kTS);
+      ++qm;
+      if (++Qm.kt >= Qm.nk) load_mpos(Qm.it + G);
+    };
+    if (ctl) {
+      load_pos(blockIdx.x);
+      for (int t = 0; t < kTS && P.it < A.nitems; ++t) issue_tma(t);
+      load_mpos(blockIdx.x);
+      mma_step();  // position 0
+    }
+    __syncwarp();
     float hi[NG][16], lo[NG][16];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
@@ -466,7 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       for (int kt = 0; kt < x.nk; ++kt, ++q) {
         const int s = q & 1;
         const uint32_t ph = (uint32_t)(q >> 1) & 1u;
-        if (!__all_sync(0xffffffffu, wait_bar(&done[s], ph, abort_flag))) { if (lane == 0) fail(); ok = false; break; }
+        if (warp == 8) {
+          if (ctl) mma_step();  // position q + 1
+          __syncwarp();
+        }
+        if (!__all_sync(0xffffffffu, wait_bar(&done[s], ph, abort_flag))) {
+          if (lane == 0) fail();
+          ok = false;
+          break;
+        }
         umma::fence_after();
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -488,40 +584,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
         __syncwarp();
         if (lane == 0) arrive(&accempty[s]);
         if (kt + 1 < x.nk) continue;
-        // ---- epilogue of the item: the accumulators go through shared memory
-        // (this thread's own slots), so that they are not live in registers
-        // while the outputs are formed
-        float* epi = reinterpret_cast<float*>(smem + Ly::kEpiOff) + (size_t)(tid - 9 * 32) * NG * 32;
-#pragma unroll
-        for (int g = 0; g < NG; ++g)
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            epi[g * 32 + j] = hi[g][j];
-            epi[g * 32 + 16 + j] = lo[g][j];
-            hi[g][j] = lo[g][j] = 0.f;
-          }
-        const volatile float* ep = epi;  // read back at the point of use (keeps few values live)
+        // ---- epilogue of the item, one group at a time: the group's
+        // accumulators go through shared memory (slot k of drain thread t at
+        // k * 256 + t, conflict-free) so that they are not live in registers
+        // while its outputs are formed
         const int row = x.t0 + 32 * qd + lane;
+        float* epi = reinterpret_cast<float*>(smem + Ly::kEpiOff) + (tid - 8 * 32);
+        const volatile float* ep = epi;
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
           if (g >= ngl) continue;
-          const SpinGroup& sg = A.groups[x.gs * NG + g];
-          const int sv = sg.s, as = sv < 0 ? -sv : sv, nb = sg.nb;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            epi[j * 256] = hi[g][j];
+            epi[(16 + j) * 256] = lo[g][j];
+            hi[g][j] = lo[g][j] = 0.f;
+          }
+          // the group's map indices for this thread's 8 (map, sign) columns,
+          // loaded together, then the outputs' addresses, loaded together
+          const SpinGroup* sgp = A.groups + (x.gs * NG + g);
+          const int sv = sgp->s, as = sv < 0 ? -sv : sv, nb = sgp->nb;
+          int mapj[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = 8 * half + jj;
+            const bool neg = j >= nb;
+            mapj[jj] = (j < 2 * nb && !(neg && x.am == 0)) ? sgp->maps[neg ? j - nb : j] : -1;
+          }
           if (DIR == 0) {
             const int l = row;
             if (l >= x.am && l < A.l1c) {
+              long long base[8];
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) base[jj] = mapj[jj] >= 0 ? A.foff[mapj[jj]] : 0;
               const double nl = ((sv & 1) ? -1.0 : 1.0) * A.nl[l];
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) {
-                const int j = 8 * half + jj;
-                if (j >= 2 * nb) continue;
-                const bool neg = j >= nb;
-                if (neg && x.am == 0) continue;
+                if (mapj[jj] < 0) continue;
+                const bool neg = 8 * half + jj >= nb;
                 const int m = neg ? -x.am : x.am;
                 double2 o = make_double2(0.0, 0.0);
                 if (l >= as) {
-                  double ar = (double)ep[g * 32 + 2 * jj] + (double)ep[g * 32 + 16 + 2 * jj];
-                  double ai = (double)ep[g * 32 + 2 * jj + 1] + (double)ep[g * 32 + 16 + 2 * jj + 1];
+                  double ar = (double)ep[(2 * jj) * 256] + (double)ep[(16 + 2 * jj) * 256];
+                  double ai = (double)ep[(2 * jj + 1) * 256] + (double)ep[(16 + 2 * jj + 1) * 256];
                   const double sg2 = (neg && (l & 1)) ? -nl : nl;
                   ar *= sg2;
                   ai *= sg2;
@@ -532,31 +637,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
                     default: o = make_double2(ai, -ar); break;
                   }
                 }
-                A.flm[A.foff[sg.maps[neg ? j - nb : j]] + (size_t)l * l + l + m] = o;
+                A.flm[base[jj] + (size_t)l * l + l + m] = o;
               }
             }
           } else {
             const int mpr = row;
             if (mpr < A.L && mpr < A.l1c) {
 #pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {
-                const int j = 8 * half + jj;
-                if (j >= 2 * nb) continue;
-                const bool neg = j >= nb;
-                if (neg && x.am == 0) continue;
-                const int b = sg.maps[neg ? j - nb : j];
-                float4* dst = reinterpret_cast<float4*>(A.Fp) + ((size_t)b * A.M + (neg ? -x.am : x.am) + A.L - 1) * A.L + mpr;
-                float rh = ep[g * 32 + 2 * jj], rl = ep[g * 32 + 16 + 2 * jj];
-                float ih = ep[g * 32 + 2 * jj + 1], il = ep[g * 32 + 16 + 2 * jj + 1];
-                if (neg && (mpr & 1)) { rh = -rh; rl = -rl; ih = -ih; il = -il; }
-                float4 cur = *dst;
-                ff_add(cur.x, cur.y, rh, rl);
-                ff_add(cur.z, cur.w, ih, il);
-                *dst = cur;
+              for (int j0 = 0; j0 < 8; j0 += 4) {  // four read-modify-writes in flight at a time
+                float4* dst[4];
+                float4 cur[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int jj = j0 + u;
+                  const bool neg = 8 * half + jj >= nb;
+                  dst[u] = reinterpret_cast<float4*>(A.Fp) +
+                           ((size_t)(mapj[jj] < 0 ? 0 : mapj[jj]) * A.M + (neg ? -x.am : x.am) + A.L - 1) * A.L + mpr;
+                  cur[u] = mapj[jj] >= 0 ? *dst[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const int jj = j0 + u;
+                  if (mapj[jj] < 0) continue;
+                  const bool neg = 8 * half + jj >= nb;
+                  float rh = ep[(2 * jj) * 256], rl = ep[(16 + 2 * jj) * 256];
+                  float ih = ep[(2 * jj + 1) * 256], il = ep[(16 + 2 * jj + 1) * 256];
+                  if (neg && (mpr & 1)) { rh = -rh; rl = -rl; ih = -ih; il = -il; }
+                  ff_add(cur[u].x, cur[u].y, rh, rl);
+                  ff_add(cur[u].z, cur[u].w, ih, il);
+                  *dst[u] = cur[u];
+                }
               }
             }
           }
         }
+      }
+    }
+    if (ctl && *abort_flag) {
+      // let the MMAs already issued finish before the TMEM is released, and
+      // the TMA loads already issued land before the CTA's shared memory goes
+      umma::commit(fin);
+      wait_bar_all(fin, 0);
+      for (int t = 0; t < kTS; ++t) {
+        const int nt = n_tma > t ? (n_tma - t - 1) / kTS + 1 : 0;  // loads issued to stage t
+        if (nt > 0) wait_bar_all(&tma_full[t], (uint32_t)(nt - 1) & 1u);
       }
     }
   }

@@ -44,12 +44,22 @@ struct TnArgs {
   const int* top_exp;       // top-row exponents
 };
 
-// x 2^E in single precision (x = the pair's high part)
-__device__ __forceinline__ float scaled(float x, int E) {
-  if (E == 0) return x;
-  if (E < -400) return 0.0f;
-  return ldexpf(x, E);
-}
+// 2^k as a float for -126 <= k <= 127 (exact, built from the exponent field)
+__device__ __forceinline__ float exp2_int(int k) { return __int_as_float((k + 127) << 23); }
+
+// The power of two 2^E of a column as two float factors f1 f2 (f1 = 2^max(E, -126),
+// f2 = the rest, 0 below 2^-252), so that x 2^E = (x f1) f2: one rounding for
+// every result in the normal range; below 2^-126 (irrelevant next to the
+// 2^-24 staging precision) the result is a denormal or zero.
+struct Scale2 {
+  float f1, f2;
+  __device__ __forceinline__ void set(int E) {
+    const int e1 = E > -126 ? E : -126;
+    f1 = exp2_int(e1);
+    f2 = (E - e1 < -126) ? 0.0f : exp2_int(E - e1);
+  }
+  __device__ __forceinline__ float apply(float x) const { return __fmul_rn(__fmul_rn(x, f1), f2); }
+};
 
 __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
   __shared__ float2 c1[kTMaxL + 1];  // 2 / b(m')
@@ -71,7 +81,9 @@ __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
   float2 cur = A.top[t0];
   float2 prev = make_float2(0.f, 0.f);
   int E = A.top_exp[t0];
-  st[(size_t)l * LD] = scaled(cur.x, E);
+  Scale2 sc;
+  sc.set(E);
+  st[(size_t)l * LD] = sc.apply(cur.x);
   const float2 mf = make_float2((float)m, 0.f);
   for (int mp = l; mp >= 1; --mp) {
     const float2 t = NumFF::mul(c1[mp], mf);    // 2 m / b
@@ -83,8 +95,9 @@ __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
       cur = make_float2(cur.x * 0x1p-64f, cur.y * 0x1p-64f);
       prev = make_float2(prev.x * 0x1p-64f, prev.y * 0x1p-64f);
       E += 64;
+      sc.set(E);
     }
-    st[(size_t)(mp - 1) * LD] = scaled(cur.x, E);
+    st[(size_t)(mp - 1) * LD] = sc.apply(cur.x);
   }
 }
 
