@@ -6,13 +6,12 @@
 // writes output k to position (j / Ns) Ns R + (j mod Ns) + k Ns; the result is in
 // natural order after the last stage.
 //
-// Radices 2, 3, 4, 5, 7 and 8 run as register butterflies: each thread loads
+// Radices 2, 3, 4, 5, 7 and 8 (and 11, 13 in single precision) run as register butterflies: each thread loads
 // the inputs of its butterflies, the block synchronises, and the outputs
 // overwrite the inputs, so one shared buffer of n elements suffices.  Other odd
 // primes (the 2L-1 lengths contain factors such as 13, 31, 73 or 127) use a
 // dot-product stage in which each output is an R-term sum (compensated in
-// FP32); no Bluestein step is needed.  The out-of-place (ping-pong) variant also has register butterflies
-// for 11 and 13 (4095 = 3^2 5 7 13 at L = 2048).  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
+// FP32); no Bluestein step is needed.  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
 #pragma once
 #include <cuda_runtime.h>
 #include "internal.h"
@@ -244,6 +243,16 @@ __device__ void fft_inplace(typename cplx<T>::t* buf, const FftDesc& d, const ty
       case 5: fftk::stage_reg<T, 5, VPT>(buf, d.n, Ns, tw, inv); break;
       case 7: fftk::stage_reg<T, 7, VPT>(buf, d.n, Ns, tw, inv); break;
       case 8: fftk::stage_reg<T, 8, VPT>(buf, d.n, Ns, tw, inv); break;
+      // 11 and 13 in registers in single precision (two butterflies of 13 double
+      // values per thread would not fit); double keeps the dot-product stage
+      case 11:
+        if constexpr (sizeof(T) == 4) fftk::stage_reg<T, 11, VPT>(buf, d.n, Ns, tw, inv);
+        else fftk::stage_dot<T, VPT>(buf, d.n, Ns, R, tw, inv);
+        break;
+      case 13:
+        if constexpr (sizeof(T) == 4) fftk::stage_reg<T, 13, VPT>(buf, d.n, Ns, tw, inv);
+        else fftk::stage_dot<T, VPT>(buf, d.n, Ns, R, tw, inv);
+        break;
       default: fftk::stage_dot<T, VPT>(buf, d.n, Ns, R, tw, inv); break;
     }
     Ns *= R;

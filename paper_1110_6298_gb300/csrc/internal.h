@@ -56,6 +56,14 @@ struct mw_plan {
   int* d_spins = nullptr;
 
   FftDesc fM{}, fN{};
+  // forward weight convolution by even lags (kernels_fft.cu): length NE of the
+  // two half convolutions, its twiddles, and the DFTs of the even-lag kernel
+  // w(2d) over the lags the even and the odd half use, pre-scaled by 1/(NE M)
+  FftDesc fE{};
+  int NE = 0;
+  void* d_twE = nullptr;
+  void* d_Ue = nullptr;
+  void* d_Uo = nullptr;
   int fft_threads = 0;             // block size of the FFT kernels
   // tables, precision of the FFT stages (double2 or float2 per entry)
   void* d_twM = nullptr;           // e^{-2 pi i k / M}, k < M

@@ -6,9 +6,9 @@
 //                   closed form to 2 pi f(pi,0) delta_{m,s}.
 //   theta_forward : one block per (m, map): periodic extension with parity
 //                   (-1)^(m+s), DFT over the 2L-1 extended nodes with the half-sample
-//                   phase e^{-i m' pi/M} (F_mm'), zero-pad to N >= 4L-3, inverse DFT,
-//                   product with the DFT of the reflected weights, DFT back
-//                   (Eq. Gmm_convolution), then the +-m' fold
+//                   phase e^{-i m' pi/M} (F_mm'), the weight convolution of
+//                   Eq. (Gmm_convolution) by its even lags (two circular
+//                   convolutions of about 1.5 L points), then the +-m' fold
 //                   G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'} used by the Wigner stage.
 // Inverse (Sec. IV-E):
 //   theta_inverse : one block per (m, map): phase (-1)^s i^-(m+s) of Eq. (Fmm),
@@ -148,72 +148,95 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_phi_forward(Dims d, FftDesc 
   }
 }
 
-template <typename T, bool PP>
-__global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward(Dims d, FftDesc fM, FftDesc fN, const C<T>* __restrict__ twM,
-                                const C<T>* __restrict__ twN, const C<T>* __restrict__ phase,
-                                const C<T>* __restrict__ V, const C<T>* __restrict__ Gt, C<T>* __restrict__ Gp,
-                                const int* __restrict__ spins) {
+// Forward theta stage by even lags.  The weights w(k) vanish at odd k except
+// k = +-1, and the w(+-1) terms drop out of every f_lm: the extended G~_m is
+// reflection-symmetric about theta = pi (G~(2 pi - theta) = (-1)^(m+s) G~(theta)),
+// so F_{m,-m''} = (-1)^(m+s) F_mm'', their contribution to G_mm' is odd under
+// m' -> -m' and cancels in the fold G+ = G_mm' + (-1)^(m+s) G_{m,-m'} (at m' = 0
+// it multiplies Delta_{0m} Delta_{0,-s}, which vanishes when m+s is odd).  With
+// even lags only, Eq. (Gmm_convolution) splits into two convolutions with the
+// kernel w(2d): even m'' = 2j into even m' = 2i, odd into odd, each a circular
+// convolution of length NE (about 1.5 L) covering the lags that occur; and the
+// even-lag G_mm' obeys the same symmetry, so G+_{m,m'} = 2 G_mm' for m' > 0 and
+// only m' >= 0 is formed.  One block per (m, map): extension, FFT_M with the
+// half-sample phase, the split into the two halves, inverse FFT_NE, product
+// with the kernel's DFT, FFT_NE, every FFT in place (2 NE complex values of
+// shared memory).
+// Forward theta stage by even lags.  The weights w(k) vanish at odd k except
+// k = +-1, and the w(+-1) terms drop out of every f_lm: the extended G~_m is
+// reflection-symmetric about theta = pi (G~(2 pi - theta) = (-1)^(m+s) G~(theta)),
+// so F_{m,-m''} = (-1)^(m+s) F_mm'', their contribution to G_mm' is odd under
+// m' -> -m' and cancels in the fold G+ = G_mm' + (-1)^(m+s) G_{m,-m'} (at m' = 0
+// it multiplies Delta_{0m} Delta_{0,-s}, which vanishes when m+s is odd).  With
+// even lags only, Eq. (Gmm_convolution) splits into two convolutions with the
+// kernel w(2d): even m'' = 2j into even m' = 2i, odd into odd, each a circular
+// convolution of length NE (about 1.5 L) covering the lags that occur; and the
+// even-lag G_mm' obeys the same symmetry, so G+_{m,m'} = 2 G_mm' for m' > 0 and
+// only m' >= 0 is formed.  One block per (m, map): extension, FFT_M with the
+// half-sample phase, the split into the two halves, inverse FFT_NE, product
+// with the kernel's DFT, FFT_NE (ping-pong FFTs; max(2M, 4 NE) complex values of
+// shared memory, against 2 N with N >= 4L-3 for the direct convolution).
+constexpr int kEvenVPT = 8;  // values of F a thread carries through the split (512 threads up to M = 4095)
+
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads) k_theta_forward_even(
+    Dims d, FftDesc fM, FftDesc fE, const C<T>* __restrict__ twM, const C<T>* __restrict__ twE,
+    const C<T>* __restrict__ phase, const C<T>* __restrict__ Ue, const C<T>* __restrict__ Uo,
+    const C<T>* __restrict__ Gt, C<T>* __restrict__ Gp, const int* __restrict__ spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
-  const int L = d.L, M = d.M, N = d.N;
+  const int L = d.L, M = d.M, NE = fE.n;
+  C<T>* X = buf;           // even half (ping-pong pair X, X + NE)
+  C<T>* Y = buf + 2 * NE;  // odd half (Y, Y + NE)
   const int im = blockIdx.x, b = blockIdx.y;
   const int m = im - (L - 1);
   const int s = spin_of(spins, b);
   const T sg = (T)parity_sign(m + s);
   const C<T>* g = Gt + ((long long)b * M + im) * L;
-  // periodic extension over the 2L-1 nodes
-  for (int t = threadIdx.x; t < M; t += blockDim.x)
-    buf[t] = (t < L) ? g[t] : cscale<T>(g[2 * L - 2 - t], sg);
+  // periodic extension over the 2L-1 nodes, FFT_M
+  for (int t = threadIdx.x; t < M; t += blockDim.x) buf[t] = (t < L) ? g[t] : cscale<T>(g[2 * L - 2 - t], sg);
   __syncthreads();
-  C<T>* res;
-  if constexpr (PP) {
-    // F_mm' (times 2 pi M, folded into V) with the half-sample phase, zero-padded to N
-    C<T>* f = fft_pp<T>(buf, buf + N, fM, twM, false);
-    C<T>* x = (f == buf) ? buf + N : buf;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      const int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
-      x[k] = (mp == 0x7fffffff) ? mkc<T>(0, 0) : cmul<T>(f[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
-    }
-    __syncthreads();
-    C<T>* y = fft_pp<T>(x, f, fN, twN, true);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) y[k] = cmul<T>(y[k], V[k]);
-    __syncthreads();
-    res = fft_pp<T>(y, (y == buf) ? buf + N : buf, fN, twN, false);
-  } else {
-    fft_inplace<T, kFftVPT>(buf, fM, twM, false);
-    C<T> v[kFftVPT];
+  const C<T>* F = fft_pp<T>(buf, buf + M, fM, twM, false);
+  // F_mm'' times the half-sample phase, split by the parity of m'' into the
+  // halves (m'' = 2j at X[j mod NE], m'' = 2j+1 at Y[j mod NE]), zero elsewhere
+  C<T> v[kEvenVPT];
 #pragma unroll
-    for (int r = 0; r < kFftVPT; ++r) {
-      const int k = threadIdx.x + r * blockDim.x;
-      if (k < N) {
-        int mp = (k <= L - 1) ? k : ((k >= N - (L - 1)) ? k - N : 0x7fffffff);
-        if (mp == 0x7fffffff) v[r] = mkc<T>(0, 0);
-        else v[r] = cmul<T>(buf[mp < 0 ? mp + M : mp], phase[mp + L - 1]);
-      }
+  for (int r = 0; r < kEvenVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < M) {
+      const int mp = (k <= L - 1) ? k : k - M;
+      v[r] = cmul<T>(F[k], phase[mp + L - 1]);
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kFftVPT; ++r) {
-      const int k = threadIdx.x + r * blockDim.x;
-      if (k < N) buf[k] = v[r];
-    }
-    __syncthreads();
-    fft_inplace<T, kFftVPT>(buf, fN, twN, true);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = cmul<T>(buf[k], V[k]);
-    __syncthreads();
-    fft_inplace<T, kFftVPT>(buf, fN, twN, false);
-    res = buf;
   }
-  // fold m' >= 0: G+_{m,0} = G_m0, G+_{m,m'} = G_mm' + (-1)^(m+s) G_{m,-m'}
+  __syncthreads();
+  for (int k = threadIdx.x; k < NE; k += blockDim.x) X[k] = Y[k] = mkc<T>(0, 0);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kEvenVPT; ++r) {
+    const int k = threadIdx.x + r * blockDim.x;
+    if (k < M) {
+      const int mp = (k <= L - 1) ? k : k - M;
+      const int j = (mp - (mp & 1)) / 2;  // floor(mp / 2)
+      const int idx = j < 0 ? j + NE : j;
+      if (mp & 1) Y[idx] = v[r];
+      else X[idx] = v[r];
+    }
+  }
+  __syncthreads();
+  C<T>* xe = fft_pp<T>(X, X + NE, fE, twE, true);
+  C<T>* xo = fft_pp<T>(Y, Y + NE, fE, twE, true);
+  for (int k = threadIdx.x; k < NE; k += blockDim.x) {
+    xe[k] = cmul<T>(xe[k], Ue[k]);
+    xo[k] = cmul<T>(xo[k], Uo[k]);
+  }
+  __syncthreads();
+  xe = fft_pp<T>(xe, xe == X ? X + NE : X, fE, twE, false);
+  xo = fft_pp<T>(xo, xo == Y ? Y + NE : Y, fE, twE, false);
+  // G+_{m,0} = G_m0, G+_{m,m'} = 2 G_mm' (m' > 0): m' = 2i from the even half, 2i+1 from the odd
   C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {
-    C<T> a = res[mp];
-    if (mp > 0) {
-      const C<T> c = res[N - mp];
-      a.x += sg * c.x;
-      a.y += sg * c.y;
-    }
-    out[mp] = a;
+    const C<T> a = (mp & 1) ? xo[mp >> 1] : xe[mp >> 1];
+    out[mp] = mp == 0 ? a : cscale<T>(a, (T)2);
   }
 }
 
@@ -512,20 +535,16 @@ cudaError_t phi_forward_t(const mw_plan* p, const void* map, cudaStream_t st) {
 }
 template <typename T>
 cudaError_t theta_forward_t(const mw_plan* p, cudaStream_t st) {
-  cudaError_t e;
-  if (pp_bytes<T>(p->N) <= kSmemMax) {
-    const int sm = pp_bytes<T>(p->N);
-    if ((e = set_smem(k_theta_forward<T, true>, sm)) != cudaSuccess) return e;
-    k_theta_forward<T, true><<<dim3(p->M, p->B), threads_pp(p->N), sm, st>>>(
-        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
-        (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
-  } else {
-    const int sm = p->N * (int)sizeof(C<T>);
-    if ((e = set_smem(k_theta_forward<T, false>, sm)) != cudaSuccess) return e;
-    k_theta_forward<T, false><<<dim3(p->M, p->B), threads_inplace(p->N), sm, st>>>(
-        dims_of(p), p->fM, p->fN, (const C<T>*)p->d_twM, (const C<T>*)p->d_twN, (const C<T>*)p->d_phase,
-        (const C<T>*)p->d_V, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
-  }
+  const int n = 2 * p->M > 4 * p->NE ? 2 * p->M : 4 * p->NE;
+  const int sm = n * (int)sizeof(C<T>);
+  cudaError_t e = set_smem(k_theta_forward_even<T>, sm);
+  if (e != cudaSuccess) return e;
+  int nt = ((p->M + kEvenVPT - 1) / kEvenVPT + 31) / 32 * 32;  // every thread carries <= kEvenVPT values of F
+  const int pp = threads_pp(p->NE > p->M ? p->NE : p->M);
+  if (nt < pp) nt = pp;
+  k_theta_forward_even<T><<<dim3(p->M, p->B), nt, sm, st>>>(
+      dims_of(p), p->fM, p->fE, (const C<T>*)p->d_twM, (const C<T>*)p->d_twE, (const C<T>*)p->d_phase,
+      (const C<T>*)p->d_Ue, (const C<T>*)p->d_Uo, (const C<T>*)p->d_Gt, (C<T>*)p->d_Gp, p->d_spins);
   return cudaGetLastError();
 }
 template <typename T>

@@ -76,7 +76,7 @@ void free_plan(mw_plan* p) {
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
                   p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff,
-                  p->d_tn_top, p->d_tn_exp, p->d_flmT, p->d_tc2_items};
+                  p->d_tn_top, p->d_tn_exp, p->d_flmT, p->d_tc2_items, p->d_twE, p->d_Ue, p->d_Uo};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -165,7 +165,23 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
       p->q_foff[b] = real ? (long long)b * L * L : p->foff[b];
     }
   }
-  if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN)) { free_plan(p); return MW_EUNSUPPORTED; }
+  {
+    // even-lag halves of the forward convolution: even m'' = 2j, |2j| <= L-1,
+    // outputs m' = 2i in [0, L-1]; odd m'' = 2j+1, outputs m' = 2i+1; a
+    // circular convolution of length NE is exact once NE covers every lag
+    // j - i that occurs
+    const int je = (L - 1) / 2;
+    const int jo_min = -(L / 2), jo_max = (L - 2) / 2;
+    const int span_e = 3 * je + 1;
+    const int span_o = jo_max >= jo_min ? jo_max - (jo_min - jo_max) + 1 : 1;
+    int NE = span_e > span_o ? span_e : span_o;
+    while (!smooth7(NE)) ++NE;
+    p->NE = NE;
+  }
+  if (!factorize(p->M, &p->fM) || !factorize(p->N, &p->fN) || !factorize(p->NE, &p->fE)) {
+    free_plan(p);
+    return MW_EUNSUPPORTED;
+  }
 
   // spin groups (order of first appearance; at most kMaxGroupMaps maps each,
   // kTcGroupMaps on the tensor-core path)
@@ -230,6 +246,37 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
       im[j] = si / ((double)N * M);
     }
     chk(dbl ? upload_complex<double>(re, im, &p->d_V) : upload_complex<float>(re, im, &p->d_V));
+  }
+  {
+    // U_k = sum_{d in [d0, d1]} w(2d) e^{-2 pi i k d / NE} / (NE M) for the even
+    // half (d = j - i, j in [-je, je], i in [0, je]) and the odd half
+    // (j in [jo_min, jo_max], i in [0, jo_max])
+    const int NE = p->NE;
+    twiddles(NE);
+    chk(dbl ? upload_complex<double>(re, im, &p->d_twE) : upload_complex<float>(re, im, &p->d_twE));
+    std::vector<double> cr(NE), ci(NE);
+    for (int x = 0; x < NE; ++x) unit_root(x, NE, &cr[x], &ci[x]);
+    const int je = (L - 1) / 2, jo_min = -(L / 2), jo_max = (L - 2) / 2;
+    auto kernel_dft = [&](int d0, int d1, void** dst) {
+      re.assign(NE, 0.0); im.assign(NE, 0.0);
+      for (int k = 0; k < NE; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (int d = d0; d <= d1; ++d) {
+          double wr, wi;
+          weight(2 * d, &wr, &wi);
+          long long x = ((long long)k * d) % NE;
+          if (x < 0) x += NE;
+          sr += wr * cr[x];
+          si += wr * ci[x];
+        }
+        re[k] = sr / ((double)NE * M);
+        im[k] = si / ((double)NE * M);
+      }
+      chk(dbl ? upload_complex<double>(re, im, dst) : upload_complex<float>(re, im, dst));
+    };
+    kernel_dft(-2 * je, je, &p->d_Ue);
+    if (jo_max >= jo_min) kernel_dft(jo_min - jo_max, jo_max, &p->d_Uo);
+    else kernel_dft(0, 0, &p->d_Uo);
   }
   }  // !sweep_only
   {
