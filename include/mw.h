@@ -117,6 +117,14 @@ enum { MW_FLAG_REAL = 1 << 9 };
  * Both agree to the FP32 staging precision the mixed contractions read. */
 enum { MW_FLAG_DELTA_TN = 1 << 10, MW_FLAG_DELTA_RISBO = 1 << 11 };
 
+/* MW_FLAG_AUTOTUNE (or-ed into flags): choose the plan's tuning (below) by
+ * measurement.  At plan creation the tuning cache named by the environment
+ * variable MW_TUNE_CACHE (a file of JSON lines, one per key) is consulted; if
+ * it holds the plan's key the recorded tuning is applied, otherwise
+ * mw_plan_autotune runs and, when MW_TUNE_CACHE is set, its choice is
+ * recorded.  Without the flag a plan starts from the defaults (512, 2, 256). */
+enum { MW_FLAG_AUTOTUNE = 1 << 12 };
+
 /* Create a plan for `batch` maps of band limit L and spin s.
  * Requires 1 <= L <= 2048, |s| < L, batch >= 1, out != NULL.  Allocates the
  * device workspace on the current CUDA device; *out is NULL on failure. */
@@ -219,9 +227,15 @@ mw_status mw_quadrature_weights(int L, int s, double *q_out, void *stream);
 mw_status mw_quadrature(mw_plan *plan, const void *maps_q, void *integrals, void *stream);
 
 /* Wait for the plan's work on `stream` and report device-side errors: returns
- * MW_ETIMEOUT (and clears the flag) if a tensor-core wait inside a kernel gave
- * up since the last check -- the affected outputs are then invalid -- MW_ECUDA
- * if the stream reports an error, MW_OK otherwise. */
+ * MW_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel (a
+ * tensor-core pipeline stage, or a neighbour's plane tile in Risbo's sweep)
+ * gave up since the last check -- the affected outputs are then invalid and
+ * the plan stays usable -- MW_ECUDA if the stream reports an error, MW_OK
+ * otherwise.  Debug environment variables, read at every launch of Risbo's
+ * sweep and never set in normal use: MW_DEBUG_STALL_PLANE=<l> makes one block
+ * of the sweep leave before plane l without publishing it, and
+ * MW_DEBUG_POLLS=<n> limits every neighbour wait to n polls, so that the
+ * timeout path can be exercised without faulting or hanging the GPU. */
 mw_status mw_plan_sync(mw_plan *plan, void *stream);
 
 /* Free a plan and its workspace.  NULL-safe.  Synchronises the device. */
@@ -253,6 +267,52 @@ int mw_plan_last_launches(const mw_plan *plan);
 enum { MW_STAGE_PHI = 0, MW_STAGE_THETA = 1, MW_STAGE_DELTA = 2, MW_STAGE_CONTRACT = 3, MW_NUM_STAGES = 4 };
 mw_status mw_plan_set_timing(mw_plan *plan, int enable);
 mw_status mw_plan_stage_times(mw_plan *plan, double *ms, long long *launches, int reset);
+
+/* Tuning (not in the paper): how the mixed-precision Wigner stage is cut into
+ * launches and passes.  None of it changes what is computed; `groups` and
+ * `tn_threads` leave results bitwise unchanged, `chunk` moves where the
+ * inverse contraction's float-float partial sums are added (differences at
+ * the 1e-7 level, inside the 1e-6 bar).
+ *   chunk       Wigner planes per recursion + contraction launch: 128, 256 or
+ *               512 (mixed precisions; the FP64 path stages 64 planes).
+ *   groups      spin groups of up to 8 maps per pass of the BF16x3
+ *               contraction pipeline: 1 or 2.
+ *   tn_threads  columns per block of the Trapani-Navaza recursion: 128 or 256.
+ *   ms          one inverse + forward of the plan's batch with these values, in
+ *               milliseconds, as measured by mw_plan_autotune (0: not measured).
+ * mw_plan_get_tuning  the plan's current values.
+ * mw_plan_set_tuning  apply values (MW_EINVAL if one is out of range; ms is
+ *                     kept as given).  Discards the plan's captured graphs.
+ * mw_plan_autotune    time every candidate (chunk x groups x tn_threads, those
+ *                     that apply to the plan's precision and recursion) with
+ *                     CUDA events on `stream` over one inverse + forward of
+ *                     the plan's batch on scratch buffers it allocates and
+ *                     frees, apply the fastest and record it in MW_TUNE_CACHE
+ *                     when that variable is set.  Synchronises `stream`.
+ * Host-only helpers (no device work), for callers that manage caches:
+ * mw_tune_key           the cache key of a plan of n maps (band limits L[b],
+ *                       spins spins[b], the plan's flags) on a device of the
+ *                       given name: the sorted multiset of (L, s), precision,
+ *                       recursion, real-signal flag and device.  MW_EINVAL if
+ *                       `len` is too small (the key is then not written).
+ * mw_tune_cache_lookup  *found = 1 and *out filled if the file at `path` holds
+ *                       `key`; *found = 0 if not, or if the file is absent.
+ * mw_tune_cache_store   add `key` with *t to the file at `path`, replacing an
+ *                       existing line of the same key (written to a temporary
+ *                       file and renamed into place).  MW_EINVAL on I/O failure. */
+typedef struct {
+  int chunk;
+  int groups;
+  int tn_threads;
+  double ms;
+} mw_tuning;
+mw_status mw_plan_get_tuning(const mw_plan *plan, mw_tuning *out);
+mw_status mw_plan_set_tuning(mw_plan *plan, const mw_tuning *t);
+mw_status mw_plan_autotune(mw_plan *plan, void *stream);
+mw_status mw_tune_key(int n, const int *L, const int *spins, unsigned flags, const char *device, char *key,
+                      size_t len);
+mw_status mw_tune_cache_lookup(const char *path, const char *key, mw_tuning *out, int *found);
+mw_status mw_tune_cache_store(const char *path, const char *key, const mw_tuning *t);
 
 /* mw_inverse_noalloc: the inverse transform of ONE map of band limit L and spin
  * s, FP64 throughout, that allocates no memory at all -- no plan, no

@@ -90,6 +90,13 @@ struct mw_plan {
   int tc2_ng = 2;
   int4* d_tc2_items = nullptr;
   std::vector<int> tc2_off;
+  int tc2_chunk = 0;               // chunk the work lists were built for
+  // tuning (mw_plan_set_tuning / mw_plan_autotune): planes per recursion +
+  // contraction launch (the sweep owner's value governs), Trapani-Navaza
+  // columns per block, and the measured round trip of the choice
+  int chunk = kTcChunk;
+  int tn_threads = 256;
+  double tuned_ms = 0.0;
 
   // workspace
   void* d_Gt = nullptr;            // [B][M][L] G_m(theta_t) (forward) / [B][L][M] F_m(theta_t) (inverse)
@@ -167,7 +174,7 @@ cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, c
 // work lists of plan p, the transposed N_l f_lm, and one chunk's contraction
 // (dir 0: Eq. flm_wig into flm; dir 1: Eq. Fmm into F+)
 cudaError_t make_tc2_tensor_maps(mw_plan* o);
-cudaError_t make_tc2_items(mw_plan* p);
+cudaError_t make_tc2_items(mw_plan* p, int chunk);
 cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st);
 cudaError_t launch_tc2(const mw_plan* p, const mw_plan* o, int dir, int l0, int l1c, double2* flm, cudaStream_t st);
 // Trapani-Navaza planes l in [lb, le) into staging slots l - l0 (mixed paths)

@@ -761,14 +761,18 @@ cudaError_t make_tc2_tensor_maps(mw_plan* o) {
 // directions, as (am, first row, group slice, K tiles), each list ordered by
 // |m| so that the items sharing one row of B run side by side (their B rows
 // meet in L2), l tiles largest first.
-cudaError_t make_tc2_items(mw_plan* p) {
+cudaError_t make_tc2_items(mw_plan* p, int chunk) {
   const int L = p->L, ng = (int)p->groups.size();
+  if (p->d_tc2_items) {
+    cudaFree(p->d_tc2_items);
+    p->d_tc2_items = nullptr;
+  }
   const int ngs = (ng + p->tc2_ng - 1) / p->tc2_ng;
   std::vector<int4> all;
   p->tc2_off.clear();
   for (int dir = 0; dir < 2; ++dir) {
-    for (int l0 = 0; l0 < L; l0 += kTcChunk) {
-      const int l1c = std::min(l0 + kTcChunk, L);
+    for (int l0 = 0; l0 < L; l0 += chunk) {
+      const int l1c = std::min(l0 + chunk, L);
       p->tc2_off.push_back((int)all.size());
       for (int am = 0; am < l1c; ++am) {
         if (dir == 0) {
@@ -788,10 +792,10 @@ cudaError_t make_tc2_items(mw_plan* p) {
     }
   }
   p->tc2_off.push_back((int)all.size());
+  p->tc2_chunk = chunk;
   if (all.empty()) return cudaSuccess;
   cudaError_t e = cudaMalloc((void**)&p->d_tc2_items, sizeof(int4) * all.size());
   if (e != cudaSuccess) return e;
-  p->ws_bytes += sizeof(int4) * all.size();
   return cudaMemcpy(p->d_tc2_items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);
 }
 
@@ -823,8 +827,8 @@ cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStrea
 // planes [l0, l1c) of the chunk that starts at l0.
 cudaError_t launch_tc2(const mw_plan* p, const mw_plan* o, int dir, int l0, int l1c, double2* flm,
                        cudaStream_t st) {
-  const int chunk = l0 / kTcChunk;
-  const int nch = (p->L + kTcChunk - 1) / kTcChunk;
+  const int chunk = l0 / p->tc2_chunk;
+  const int nch = (p->L + p->tc2_chunk - 1) / p->tc2_chunk;
   const int k = dir * nch + chunk;
   const int4* items = p->d_tc2_items + p->tc2_off[k];
   const int n = p->tc2_off[k + 1] - p->tc2_off[k];

@@ -16,7 +16,7 @@
 // from a host table of (float-float mantissa, exponent) pairs.
 //
 // Planes are independent given their top rows, and so are the columns of a
-// plane: one thread per column, one block per (plane, 256 columns), no waits
+// plane: one thread per column, one block per (plane, 128 or 256 columns), no waits
 // between blocks.  A block first forms the plane's recursion coefficients
 // 2/b(m') and a(m')/b(m') in shared memory (b = sqrt((l+m')(l-m'+1)),
 // a = sqrt((l-m')(l+m'+1))); each step then costs one float-float product by
@@ -31,7 +31,7 @@
 
 namespace {
 
-constexpr int kTThreads = 256;
+constexpr int kTThreads = 256;  // largest block (columns per block: 128 or 256, chosen by the plan)
 constexpr int kTMaxL = 2048;
 
 struct TnArgs {
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
   __shared__ float2 c1[kTMaxL + 1];  // 2 / b(m')
   __shared__ float2 c2[kTMaxL + 1];  // a(m') / b(m')
   const int l = lb + (int)blockIdx.y;
-  const int m0 = (int)blockIdx.x * kTThreads;
+  const int m0 = (int)(blockIdx.x * blockDim.x);
   if (m0 > l) return;  // whole block past the plane's last column (uniform)
-  for (int mp = 1 + (int)threadIdx.x; mp <= l; mp += kTThreads) {
+  for (int mp = 1 + (int)threadIdx.x; mp <= l; mp += (int)blockDim.x) {
     const float2 ib = NumFF::mul(A.rsq[l + mp], A.rsq[l - mp + 1]);
     c1[mp] = make_float2(2.0f * ib.x, 2.0f * ib.y);  // exact
     c2[mp] = NumFF::mul(NumFF::mul(A.sq[l - mp], A.sq[l + mp + 1]), ib);
@@ -115,7 +115,8 @@ cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st)
   a.rsq = p->d_rsqrt_ff;
   a.top = p->d_tn_top;
   a.top_exp = p->d_tn_exp;
-  const dim3 grid((le - 1) / kTThreads + 1, le - lb);
-  k_tn_planes<<<grid, kTThreads, 0, st>>>(a, lb);
+  const int nt = (p->tn_threads == 128 || p->tn_threads == 256) ? p->tn_threads : kTThreads;
+  const dim3 grid((le - 1) / nt + 1, le - lb);
+  k_tn_planes<<<grid, nt, 0, st>>>(a, lb);
   return cudaGetLastError();
 }

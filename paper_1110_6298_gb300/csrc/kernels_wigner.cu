@@ -118,6 +118,9 @@ struct RisboArgs {
   int* err;
   const int* perm;    // rank of each block in the tile assignment (null: blockIdx.x)
   int* smid_out;      // when set: record each block's SM id (placement probe)
+  unsigned polls;     // poll limit of a neighbour wait
+  int stall_l;        // debug: the block of rank stall_rank leaves before plane stall_l (-1: never)
+  int stall_rank;
 };
 
 // Value of the integer plane Delta^{l-1} (j = l-1, quarter storage, lower
@@ -138,11 +141,11 @@ __device__ __forceinline__ typename Nm::T prev_val(const typename Nm::T* __restr
 // Tile (I, J), J <= I, of the lower triangle has linear index I (I+1)/2 + J.
 __device__ __forceinline__ int tile_index(int I, int J) { return I * (I + 1) / 2 + J; }
 
-// Wait until tile t has published step `step` (bounded; returns false on timeout).
-// The first polls spin (a neighbour of the same wavefront is usually about to
-// publish); later ones back off with a short sleep.
-__device__ __forceinline__ bool wait_tile(const int* prog, int t, int step) {
-  for (unsigned polls = 0; polls < kBarrierPolls; ++polls) {
+// Wait until tile t has published step `step` (bounded by max_polls; returns
+// false on timeout).  The first polls spin (a neighbour of the same wavefront
+// is usually about to publish); later ones back off with a short sleep.
+__device__ __forceinline__ bool wait_tile(const int* prog, int t, int step, unsigned max_polls) {
+  for (unsigned polls = 0; polls < max_polls; ++polls) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(prog + t) : "memory");
     if (v >= step) return true;
@@ -202,6 +205,9 @@ __global__ void __launch_bounds__(kRThreads, 5) k_risbo_sweep(RisboArgs A, int l
   // FP64 pipes of the SMs the first block indices land on.
   const int vrank = A.perm ? A.perm[blockIdx.x] : (int)blockIdx.x;
   for (int l = l_begin; l < l_end; ++l) {
+    // debug fault injection on the host's request: this block leaves without
+    // publishing, so its neighbours' bounded waits run out (no trap, no fault)
+    if (l == A.stall_l && vrank == A.stall_rank) return;
     const int th = 2 * l - 1, ti = 2 * l;  // twice j' of the half and the integer plane
     const int nh = l, nnew = l + 1;        // sizes of the half plane and the new integer plane
     const V* d = static_cast<const V*>(A.S) + (size_t)((l - 1) % A.nslot) * plane;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(kRThreads, 5) k_risbo_sweep(RisboArgs A, int l
           const int Ii = II[k] + q / 3 - 1, Jj = JJ[k] + q % 3 - 1;
           if (Ii >= 0 && Jj >= 0 && Ii < Tp && Jj < Tp) {  // part of plane l-1
             const int hi = Ii > Jj ? Ii : Jj, lo = Ii > Jj ? Jj : Ii;
-            if (!wait_tile(A.prog, tile_index(hi, lo), l - 1)) { ok = 0; atomicOr(A.err, 2); }
+            if (!wait_tile(A.prog, tile_index(hi, lo), l - 1, A.polls)) { ok = 0; atomicOr(A.err, 2); }
           }
         }
         ok = __all_sync(0xffffffffu, ok);
@@ -467,6 +473,28 @@ cudaError_t launch_risbo(mw_plan* p, void* S, int nslot, float* S32, int l0, int
   a.rscale = ff ? (const void*)p->d_rscale_ff : (const void*)p->d_rscale;
   a.prog = p->d_prog; a.err = p->d_err;
   a.perm = p->d_perm; a.smid_out = nullptr;
+  // Debug knobs, read at every launch (never set in normal use):
+  // MW_DEBUG_STALL_PLANE=<l> makes block rank 0 leave before plane l without
+  // publishing it, MW_DEBUG_POLLS=<n> shortens every neighbour wait to n polls;
+  // together they exercise the timeout path (MW_ETIMEOUT from mw_plan_sync).
+  a.polls = kBarrierPolls;
+  a.stall_l = -1;
+  a.stall_rank = 0;
+  if (const char* v = getenv("MW_DEBUG_STALL_PLANE")) a.stall_l = atoi(v);
+  if (const char* v = getenv("MW_DEBUG_POLLS")) {
+    const long n = atol(v);
+    if (n >= 1 && n <= (long)kBarrierPolls) a.polls = (unsigned)n;
+  }
+  // every block of the persistent sweep must be resident at once (their waits
+  // depend on one another): checked before the cooperative launch
+  {
+    int per_sm = 0, nsm = 0;
+    const void* k = sweep_kernel(p->prec);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRThreads, (size_t)kRisboSmem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    if ((long)per_sm * nsm < (long)p->risbo_grid) return cudaErrorCooperativeLaunchTooLarge;
+  }
   void* args[] = {&a, &lb, &le};
   e = cudaLaunchCooperativeKernel(sweep_kernel(p->prec), dim3(p->risbo_grid), dim3(kRThreads), args,
                                   (size_t)kRisboSmem, st);
@@ -482,7 +510,14 @@ cudaError_t launch_risbo(mw_plan* p, void* S, int nslot, float* S32, int l0, int
 // with L > l: Delta^l depends on neither L nor s.
 cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {
   const bool fp64 = o->prec == MW_PREC_FP64;
-  const int chunk = fp64 ? kChunk : kTcChunk;
+  const int chunk = fp64 ? kChunk : o->chunk;
+  for (int c = 0; c < nj; ++c) {  // work lists built for another chunk (after a tuning change)
+    mw_plan* q = jobs[c].q;
+    if (!fp64 && q->prec == MW_PREC_MIXED_BF16X3 && q->tc2_chunk != chunk) {
+      cudaError_t ee = make_tc2_items(q, chunk);
+      if (ee != cudaSuccess) return ee;
+    }
+  }
   int nl = 0;
   cudaError_t e;
   for (int c = 0; c < nj; ++c) {
@@ -571,6 +606,8 @@ cudaError_t make_risbo_perm(mw_plan* p) {
   RisboArgs a{};
   a.LD = p->LD;
   a.smid_out = d_smid;
+  a.polls = kBarrierPolls;
+  a.stall_l = -1;
   int lb = 1, le = 1;  // no planes: the launch only records the placement
   void* args[] = {&a, &lb, &le};
   e = cudaLaunchCooperativeKernel(sweep_kernel(p->prec), dim3(G), dim3(kRThreads), args, (size_t)kRisboSmem, 0);

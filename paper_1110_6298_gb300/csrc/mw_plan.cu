@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -104,7 +105,7 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   const int prec = (int)(flags & 0xffu);
   if (prec != MW_PREC_FP64 && prec != MW_PREC_MIXED && prec != MW_PREC_MIXED_TF32X3) return MW_EINVAL;
   if (flags & ~(0xffu | (unsigned)MW_FLAG_GRAPH | (unsigned)MW_FLAG_REAL | (unsigned)MW_FLAG_DELTA_TN |
-                (unsigned)MW_FLAG_DELTA_RISBO))
+                (unsigned)MW_FLAG_DELTA_RISBO | (unsigned)MW_FLAG_AUTOTUNE))
     return MW_EINVAL;
   if ((flags & MW_FLAG_DELTA_TN) && (flags & MW_FLAG_DELTA_RISBO)) return MW_EINVAL;
   if ((flags & MW_FLAG_DELTA_TN) && prec == MW_PREC_FP64) return MW_EUNSUPPORTED;
@@ -418,9 +419,9 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
     // spin groups per pass of the contraction pipeline: 2 (both groups of a
     // plane tile in one pass) unless MW_TC2_GROUPS=1; results do not depend on it
     if (const char* env = getenv("MW_TC2_GROUPS")) p->tc2_ng = (atoi(env) == 1) ? 1 : 2;
-    p->ws_bytes = ws;
-    chk(make_tc2_items(p));
-    ws = p->ws_bytes;
+    p->chunk = owner ? owner->chunk : p->chunk;
+    p->tn_threads = owner ? owner->tn_threads : p->tn_threads;
+    chk(make_tc2_items(p, p->chunk));
   }
   if (e != cudaSuccess) {
     const mw_status st = from_cuda(e);
@@ -463,6 +464,15 @@ mw_status ensure_twins(mw_plan* p) {
       }
       p->twins.clear();
       return st;
+    }
+    if (t->prec == MW_PREC_MIXED_BF16X3 && t->tc2_ng != q->tc2_ng) {  // the source plan's tuning
+      t->tc2_ng = q->tc2_ng;
+      const cudaError_t e = make_tc2_items(t, p->chunk);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(t);
+        return from_cuda(e);
+      }
     }
     p->twins.push_back(t);
     p->ws_bytes += t->ws_bytes;
@@ -696,6 +706,165 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   return MW_OK;
 }
 
+// ---- tuning ----------------------------------------------------------------
+
+// Plans whose contraction work lists follow p's sweep: p itself (or its ragged
+// sub-plans) and the twins of fused calls.
+std::vector<mw_plan*> tuning_targets(mw_plan* p) {
+  std::vector<mw_plan*> v;
+  if (p->subs.empty()) v.push_back(p);
+  for (mw_plan* c : p->subs) v.push_back(c);
+  for (mw_plan* c : p->twins) v.push_back(c);
+  return v;
+}
+
+bool tuning_valid(const mw_tuning& t) {
+  return (t.chunk == 128 || t.chunk == 256 || t.chunk == 512) && (t.groups == 1 || t.groups == 2) &&
+         (t.tn_threads == 128 || t.tn_threads == 256);
+}
+
+void drop_graphs(mw_plan* p) {
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
+}
+
+mw_status apply_tuning(mw_plan* p, const mw_tuning& t) {
+  if (!tuning_valid(t)) return MW_EINVAL;
+  p->chunk = t.chunk;
+  p->tn_threads = t.tn_threads;
+  p->tuned_ms = t.ms;
+  for (mw_plan* q : tuning_targets(p)) {
+    q->chunk = t.chunk;
+    q->tn_threads = t.tn_threads;
+    q->tc2_ng = t.groups;
+    if (q->prec == MW_PREC_MIXED_BF16X3) {
+      const cudaError_t e = make_tc2_items(q, t.chunk);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+      }
+    }
+  }
+  drop_graphs(p);
+  return MW_OK;
+}
+
+mw_tuning current_tuning(const mw_plan* p) {
+  mw_tuning t;
+  t.chunk = p->chunk;
+  t.tn_threads = p->tn_threads;
+  t.groups = p->subs.empty() ? p->tc2_ng : p->subs[0]->tc2_ng;
+  t.ms = p->tuned_ms;
+  return t;
+}
+
+// Time every candidate over one inverse + forward of the plan's batch on
+// scratch buffers (one warm-up round trip, then two timed), keep the fastest.
+mw_status autotune(mw_plan* p, cudaStream_t st) {
+  const bool real = p->real;
+  const size_t map_b = (size_t)p->map_elems * (real ? sizeof(double) : sizeof(double2));
+  const size_t flm_b = (size_t)p->flm_elems * sizeof(double2);
+  void *dmap = nullptr, *dflm = nullptr;
+  cudaError_t e = cudaMalloc(&dmap, map_b);
+  if (e == cudaSuccess) e = cudaMalloc(&dflm, flm_b);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dflm, 0, flm_b, st);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  std::vector<mw_tuning> cand;
+  const mw_tuning base = current_tuning(p);
+  const bool bf16 = p->prec == MW_PREC_MIXED_BF16X3, mixed = p->prec != MW_PREC_FP64;
+  const bool tn = (p->flags & MW_FLAG_DELTA_TN) != 0;
+  size_t maxg = 0;
+  for (mw_plan* q : tuning_targets(p)) maxg = q->groups.size() > maxg ? q->groups.size() : maxg;
+  cand.push_back(base);
+  if (mixed) {
+    for (int chunk : {512, 256, 128})
+      for (int g : {2, 1})
+        for (int t : {256, 128}) {
+          if (chunk < 512 && chunk >= p->L) continue;        // one chunk either way
+          if (g == 1 && (!bf16 || maxg < 2)) continue;       // one group per pass only matters with two
+          if (t == 128 && !tn) continue;                     // the Risbo sweep has no such knob
+          mw_tuning c{chunk, g, t, 0.0};
+          if (c.chunk == base.chunk && c.groups == base.groups && c.tn_threads == base.tn_threads) continue;
+          cand.push_back(c);
+        }
+  }
+  const unsigned saved = p->flags;
+  const bool saved_timing = p->timing;
+  p->flags &= ~(unsigned)MW_FLAG_GRAPH;
+  p->timing = false;
+  int best = -1;
+  float best_ms = 0.f;
+  for (size_t i = 0; e == cudaSuccess && i < cand.size(); ++i) {
+    if (apply_tuning(p, cand[i]) != MW_OK) { e = cudaErrorUnknown; break; }
+    mw_status s1 = run(p, kInverse, dflm, dmap, st);
+    if (s1 == MW_OK) s1 = run(p, kForward, dmap, dflm, st);
+    if (s1 == MW_OK && cudaEventRecord(a, st) != cudaSuccess) s1 = MW_ECUDA;
+    for (int r = 0; r < 2 && s1 == MW_OK; ++r) {
+      s1 = run(p, kInverse, dflm, dmap, st);
+      if (s1 == MW_OK) s1 = run(p, kForward, dmap, dflm, st);
+    }
+    float ms = 0.f;
+    if (s1 == MW_OK) e = cudaEventRecord(b, st);
+    if (s1 == MW_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (s1 == MW_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (s1 != MW_OK) { e = cudaErrorUnknown; break; }
+    cand[i].ms = ms / 2.0;
+    if (best < 0 || ms < best_ms) { best = (int)i; best_ms = ms; }
+  }
+  p->flags = saved;
+  p->timing = saved_timing;
+  mw_status st_out = from_cuda(e);
+  if (best >= 0) {
+    const mw_status s2 = apply_tuning(p, cand[best]);
+    if (st_out == MW_OK) st_out = s2;
+  } else {
+    apply_tuning(p, base);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (dmap) cudaFree(dmap);
+  if (dflm) cudaFree(dflm);
+  if (st_out != MW_OK) cudaGetLastError();
+  return st_out;
+}
+
+// The cache key of plan p (its maps, precision, recursion, real flag, device).
+mw_status plan_key(const mw_plan* p, std::string* key) {
+  std::vector<int> Ls, ss;
+  if (!p->q_L.empty()) { Ls = p->q_L; ss = p->q_s; }
+  if (Ls.empty()) return MW_EINVAL;
+  cudaDeviceProp prop;
+  const char* dev = "unknown";
+  if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) dev = prop.name;
+  else cudaGetLastError();
+  std::vector<char> buf(64 + 24 * Ls.size() + 256);
+  const mw_status s = mw_tune_key((int)Ls.size(), Ls.data(), ss.data(), p->flags, dev, buf.data(), buf.size());
+  if (s == MW_OK) *key = buf.data();
+  return s;
+}
+
+// MW_FLAG_AUTOTUNE at creation: the cached tuning of the plan's key, or a
+// search (recorded when MW_TUNE_CACHE is set).
+mw_status tune_at_creation(mw_plan* p) {
+  const char* path = getenv("MW_TUNE_CACHE");
+  std::string key;
+  if (plan_key(p, &key) != MW_OK) return MW_EINVAL;
+  if (path && *path) {
+    mw_tuning t;
+    int found = 0;
+    if (mw_tune_cache_lookup(path, key.c_str(), &t, &found) == MW_OK && found && tuning_valid(t))
+      return apply_tuning(p, t);
+  }
+  mw_status s = autotune(p, 0);
+  if (s == MW_OK && path && *path) {
+    const mw_tuning t = current_tuning(p);
+    mw_tune_cache_store(path, key.c_str(), &t);  // a cache that cannot be written only costs a later search
+  }
+  return s;
+}
+
 // Ragged plan: n maps with their own band limits and spins.  The parent owns
 // the recursion state sized for max L; one sub-plan per distinct band limit
 // owns that band limit's tables and buffers and reads/writes its maps at their
@@ -823,23 +992,58 @@ mw_status mw_plan_stage_times(mw_plan* plan, double* ms, long long* launches, in
   return from_cuda(e);
 }
 
+// A freshly built plan: with MW_FLAG_AUTOTUNE, its tuning from the cache or a search.
+static mw_status finish_plan(mw_plan** out, mw_status st) {
+  if (st != MW_OK || !(*out) || !((*out)->flags & MW_FLAG_AUTOTUNE)) return st;
+  st = tune_at_creation(*out);
+  if (st != MW_OK) {
+    cudaDeviceSynchronize();
+    free_plan(*out);
+    *out = nullptr;
+  }
+  return st;
+}
+
 mw_status mw_plan_create(mw_plan** out, int L, int s, int batch, unsigned flags) {
   if (!out) return MW_EINVAL;
   *out = nullptr;
   if (batch < 1 || batch > (1 << 20)) return MW_EINVAL;
   std::vector<int> spins(batch, s);
-  return build_plan(out, L, batch, spins.data(), flags);
+  return finish_plan(out, build_plan(out, L, batch, spins.data(), flags));
 }
 
 mw_status mw_plan_create_ragged(mw_plan** out, int n, const int* L, const int* spins, unsigned flags) {
-  return build_ragged(out, n, L, spins, flags);
+  return finish_plan(out, build_ragged(out, n, L, spins, flags));
 }
 
 mw_status mw_plan_create_spins(mw_plan** out, int L, int batch, const int* spins, unsigned flags) {
   if (!out) return MW_EINVAL;
   *out = nullptr;
   if (batch < 1 || batch > (1 << 20) || !spins) return MW_EINVAL;
-  return build_plan(out, L, batch, spins, flags);
+  return finish_plan(out, build_plan(out, L, batch, spins, flags));
+}
+
+mw_status mw_plan_get_tuning(const mw_plan* plan, mw_tuning* out) {
+  if (!plan || !out) return MW_EINVAL;
+  *out = current_tuning(plan);
+  return MW_OK;
+}
+
+mw_status mw_plan_set_tuning(mw_plan* plan, const mw_tuning* t) {
+  if (!plan || !t || !tuning_valid(*t)) return MW_EINVAL;
+  return apply_tuning(plan, *t);
+}
+
+mw_status mw_plan_autotune(mw_plan* plan, void* stream) {
+  if (!plan) return MW_EINVAL;
+  const mw_status st = autotune(plan, (cudaStream_t)stream);
+  const char* path = getenv("MW_TUNE_CACHE");
+  std::string key;
+  if (st == MW_OK && path && *path && plan_key(plan, &key) == MW_OK) {
+    const mw_tuning t = current_tuning(plan);
+    mw_tune_cache_store(path, key.c_str(), &t);
+  }
+  return st;
 }
 
 mw_status mw_forward(mw_plan* plan, const void* map_in, void* flm_out, void* stream) {

@@ -20,11 +20,22 @@ FLAG_GRAPH = 1 << 8
 FLAG_REAL = 1 << 9
 FLAG_DELTA_TN = 1 << 10
 FLAG_DELTA_RISBO = 1 << 11
+FLAG_AUTOTUNE = 1 << 12
 # Wigner-plane recursion: None = the library's default (Trapani-Navaza on the
 # mixed precisions, Risbo on FP64); "tn" (mixed only) or "risbo" to choose
 DELTA = {None: 0, "tn": FLAG_DELTA_TN, "risbo": FLAG_DELTA_RISBO}
 
 _lib = None
+
+
+class Tuning(ctypes.Structure):
+    """mw_tuning: planes per recursion + contraction launch, spin groups per
+    contraction pass, Trapani-Navaza columns per block, measured ms."""
+    _fields_ = [("chunk", ctypes.c_int), ("groups", ctypes.c_int), ("tn_threads", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"chunk": self.chunk, "groups": self.groups, "tn_threads": self.tn_threads, "ms": self.ms}
 
 
 class MWError(RuntimeError):
@@ -93,6 +104,20 @@ def lib():
             getattr(L, name).restype = ll
         L.mw_layout_ragged.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ll), ctypes.POINTER(ll)]
         L.mw_layout_ragged.restype = c_int
+        L.mw_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.mw_plan_get_tuning.restype = c_int
+        L.mw_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+        L.mw_plan_set_tuning.restype = c_int
+        L.mw_plan_autotune.argtypes = [vp, vp]
+        L.mw_plan_autotune.restype = c_int
+        L.mw_tune_key.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_uint, ctypes.c_char_p,
+                                  ctypes.c_char_p, c_size]
+        L.mw_tune_key.restype = c_int
+        L.mw_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Tuning),
+                                           ctypes.POINTER(c_int)]
+        L.mw_tune_cache_lookup.restype = c_int
+        L.mw_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Tuning)]
+        L.mw_tune_cache_store.restype = c_int
         _lib = L
     return _lib
 
@@ -122,6 +147,34 @@ def layout_ragged(Ls):
     return list(mo), list(fo)
 
 
+def tune_key(Ls, spins, flags, device):
+    """The tuning-cache key of a plan of maps (Ls[b], spins[b]) with `flags` on
+    the named device (host-only)."""
+    n = len(Ls)
+    buf = ctypes.create_string_buffer(64 + 24 * n + 256)
+    st = lib().mw_tune_key(n, (ctypes.c_int * n)(*Ls), (ctypes.c_int * n)(*spins), int(flags),
+                           device.encode(), buf, len(buf))
+    if st != MW_OK:
+        raise MWError(st, "mw_tune_key")
+    return buf.value.decode()
+
+
+def tune_cache_lookup(path, key):
+    """The tuning stored under `key` in the cache file, or None."""
+    t, found = Tuning(), ctypes.c_int(0)
+    st = lib().mw_tune_cache_lookup(str(path).encode(), key.encode(), ctypes.byref(t), ctypes.byref(found))
+    if st != MW_OK:
+        raise MWError(st, "mw_tune_cache_lookup")
+    return t.as_dict() if found.value else None
+
+
+def tune_cache_store(path, key, chunk, groups, tn_threads, ms=0.0):
+    st = lib().mw_tune_cache_store(str(path).encode(), key.encode(),
+                                   ctypes.byref(Tuning(int(chunk), int(groups), int(tn_threads), float(ms))))
+    if st != MW_OK:
+        raise MWError(st, "mw_tune_cache_store")
+
+
 def quadrature_size(L):
     """Samples of a map in the quadrature layout: L(L-1) + 1."""
     return int(L) * (int(L) - 1) + 1
@@ -145,7 +198,7 @@ def _stream_of(t):
 class Plan:
     """A transform plan: L, one spin per map (or one spin for all), precision."""
 
-    def __init__(self, L, spins, batch=None, precision="fp64", graph=False, delta=None):
+    def __init__(self, L, spins, batch=None, precision="fp64", graph=False, delta=None, autotune=False):
         if isinstance(spins, int):
             if batch is None:
                 batch = 1
@@ -157,7 +210,7 @@ class Plan:
         self.precision = precision
         h = ctypes.c_void_p()
         arr = (ctypes.c_int * len(spins))(*spins)
-        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0) | DELTA[delta]
+        flags = PRECISIONS[precision] | (FLAG_GRAPH if graph else 0) | DELTA[delta] | (FLAG_AUTOTUNE if autotune else 0)
         st = lib().mw_plan_create_spins(ctypes.byref(h), self.L, self.batch, arr, flags)
         if st != MW_OK:
             raise MWError(st, "mw_plan_create_spins")
@@ -187,6 +240,30 @@ class Plan:
         n = int(lib().mw_plan_batch(h))
         return [(int(lib().mw_plan_band_limit(h, b)), int(lib().mw_plan_spin(h, b)),
                  int(lib().mw_plan_map_offset(h, b)), int(lib().mw_plan_flm_offset(h, b))) for b in range(n)]
+
+    @property
+    def tuning(self):
+        """The plan's tuning as a dict (chunk, groups, tn_threads, ms)."""
+        t = Tuning()
+        st = lib().mw_plan_get_tuning(self._h, ctypes.byref(t))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, chunk, groups, tn_threads, ms=0.0):
+        t = Tuning(int(chunk), int(groups), int(tn_threads), float(ms))
+        st = lib().mw_plan_set_tuning(self._h, ctypes.byref(t))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_set_tuning")
+
+    def autotune(self, stream=None):
+        """Time the tuning candidates on this plan's shapes and keep the fastest."""
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        st = lib().mw_plan_autotune(self._h, ctypes.c_void_p(stream))
+        if st != MW_OK:
+            raise MWError(st, "mw_plan_autotune")
+        return self.tuning
 
     @property
     def workspace_bytes(self):

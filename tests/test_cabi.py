@@ -81,6 +81,7 @@ def test_binding_constants_match_header():
     assert c["MW_FLAG_REAL"] == mw.FLAG_REAL
     assert c["MW_FLAG_DELTA_TN"] == mw.FLAG_DELTA_TN == mw.DELTA["tn"]
     assert c["MW_FLAG_DELTA_RISBO"] == mw.FLAG_DELTA_RISBO == mw.DELTA["risbo"]
+    assert c["MW_FLAG_AUTOTUNE"] == mw.FLAG_AUTOTUNE
     assert c["MW_PREC_FP64"] == mw.PRECISIONS["fp64"]
     assert c["MW_PREC_MIXED_BF16X3"] == mw.PRECISIONS["mixed"] == mw.PRECISIONS["mixed_bf16"]
     assert c["MW_PREC_MIXED_TF32X3"] == mw.PRECISIONS["mixed_tf32"]
@@ -102,7 +103,7 @@ def test_flag_rules_checked_before_device_work(libmw):
     ss = (ctypes.c_int * 2)(0, 0)
     assert libmw.mw_plan_create_ragged(ctypes.byref(h), 2, Ls, ss, mixed | real) == c["MW_EINVAL"]
     # an unknown flag bit
-    assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, mixed | (1 << 12)) == c["MW_EINVAL"]
+    assert libmw.mw_plan_create(ctypes.byref(h), 8, 0, 1, mixed | (1 << 13)) == c["MW_EINVAL"]
     assert not h.value
 
 
