@@ -383,7 +383,10 @@ def run_ours(args, rank, world, local_rank):
     # planes per launch, spin groups per contraction pass and Trapani-Navaza
     # block size, timed on this GPU before the timed region)
     t_tune = time.perf_counter()
-    plan = mw.Plan(L, spins, precision=args.precision, graph=True, autotune=not args.no_autotune)
+    plan = mw.Plan(L, spins, precision=args.precision, graph=True,
+                   autotune=not (args.no_autotune or args.tuning))
+    if args.tuning:
+        plan.set_tuning(*[int(x) for x in args.tuning.split(",")])
     t_tune = time.perf_counter() - t_tune
     tuning = plan.tuning
     maps = torch.empty((B, nmw), dtype=torch.complex128, device=dev)
@@ -399,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- the plain FP64 GPU path on the identical workload and protocol
     fp64_line = None
     acc = {}
-    if args.precision != "fp64" and not args.no_fp64_arm:
+    if args.precision != "fp64" and not args.no_fp64_arm and not args.headline_only:
         p64 = mw.Plan(L, spins, precision="fp64", graph=True)
         maps64 = torch.empty_like(maps)
         out64 = torch.empty_like(out)
@@ -427,6 +430,10 @@ def run_ours(args, rank, world, local_rank):
                      "what": "the same round trip on an MW_PREC_FP64 plan (FP64 FFTs, FP64 Risbo sweep, "
                              "DMMA contraction), graph-replayed, CUDA events, same steps"}
     torch.cuda.synchronize(dev)
+
+    if args.headline_only:
+        return headline_only_result(args, world, value, ms, K, W, L, B, stages, launches_per_step, ck, err_report,
+                                    tuning)
 
     # ---- separate forward and inverse rates
     inv_ms, _ = timed(lambda: plan.inverse(flm, out=maps), K)
@@ -484,6 +491,40 @@ def run_ours(args, rank, world, local_rank):
                    "ms_per_step": rb_ms / K, "rel_err": rb_err, "stage_ms_per_step": rb_stages,
                    "what": "the same round trip with Risbo's recursion (MW_FLAG_DELTA_RISBO)"}
 
+    # ---- a prime 2L-1: L = 2047 (4093) runs its ring and theta DFTs by
+    # Bluestein's convolution; its phi + theta time against L = 2048's
+    pr_line = None
+    if L == 2048 and not args.no_configs:
+        wp = wl.workload_l2048_b16(L=2047)
+        fp = torch.from_numpy(np.stack(wp["flm"])).to(dev)
+        pp = mw.Plan(2047, spins, precision=args.precision, graph=True)
+        mp = torch.empty((B, mw.map_size(2047)), dtype=torch.complex128, device=dev)
+        op = torch.empty_like(fp)
+
+        def rt_p():
+            pp.inverse(fp, out=mp)
+            pp.forward(mp, out=op)
+        for _ in range(W):
+            rt_p()
+        torch.cuda.synchronize(dev)
+        pr_ms, _ = timed(rt_p, K)
+        pr_err = float((op - fp).abs().max().item() / fp.abs().max().item())
+        pp.set_timing(True)
+        pp.stage_times(reset=True)
+        for _ in range(2):
+            pp.inverse(fp, out=mp)
+            pp.forward(mp, out=op)
+        torch.cuda.synchronize(dev)
+        pr_st = {k: v[0] / 2 for k, v in pp.stage_times(reset=True).items()}
+        pr_line = {"value": whole_job_value(world, B, K, pr_ms / 1e3), "unit": "transforms/s",
+                   "ms_per_step": pr_ms / K, "rel_err": pr_err, "bluestein": pp.fft_bluestein,
+                   "stage_ms_per_step": pr_st,
+                   "phi_theta_ms_vs_l2048": (pr_st["phi"] + pr_st["theta"]) / (stages["phi"] + stages["theta"]),
+                   "what": "the same round trip at L=2047, whose 2L-1 = 4093 is prime: ring and theta DFTs by "
+                           "Bluestein's convolution of length 8192"}
+        pp.close()
+        del pp, fp, mp, op
+
     # ---- end to end: the round trip through the C ABI with pinned host
     # buffers, host<->device copies inside the timed region, every step
     flm_pin = flm_h.pin_memory()
@@ -535,8 +576,8 @@ def run_ours(args, rank, world, local_rank):
         a_t = tc_flops / t["contract"] / 1e12
         a_b = c_bytes / t["contract"] / 1e9
         t_tensor, t_hbm = tc_flops / (tc_peak * 1e12), c_bytes / (pk_hbm * 1e9)
-        kern = {"mixed": "k_tc_forward/k_tc_inverse", "mixed_tf32": "k_tc_forward/k_tc_inverse (TF32)"}.get(
-            args.precision, "k_dmma_forward/k_dmma_inverse")
+        kern = {"mixed": "k_tc2 (BF16x3 pipeline, both directions)",
+                "mixed_tf32": "k_tc_forward/k_tc_inverse (TF32x3)"}.get(args.precision, "k_dmma_forward/k_dmma_inverse")
         tensor = {"achieved": a_t, "peak": tc_peak, "unit": "TFLOP/s", "frac": a_t / tc_peak,
                   "work": "4 flops per (l, m, m' >= 0, map) multiply-add, both directions",
                   "peak_src": {"mixed": "measured (MEASURED_PEAKS.json bf16 dense burst)",
@@ -587,7 +628,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"MW round trip (inverse then forward) L={L}, B={B} (8 maps s=0, 8 maps s=2)",
                    "L": L, "batch": B, "precision": args.precision,
                    "l2_flush": "inputs larger than L2", "graph": True, "parallelism": f"replicas x{world}",
-                   "tuning": dict(tuning, autotuned=not args.no_autotune, search_s=round(t_tune, 2))},
+                   "tuning": dict(tuning, autotuned=not (args.no_autotune or args.tuning),
+                                  search_s=round(t_tune, 2))},
         "gpu_launches": launches_per_step * K,
         "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": bytes_flm + bytes_map,
                 "d2h_bytes_per_step": bytes_map + bytes_flm, "steps": K, "rel_err": e2e_err,
@@ -604,6 +646,7 @@ def run_ours(args, rank, world, local_rank):
                  "ms_per_step": r_ms / K, "rel_err": r_err,
                  "what": f"round trip of {B} real spin-0 maps (Sec. IV-G), uniform[-1,1] coefficients"},
         "risbo": rb_line,
+        "prime_l2047": pr_line,
         "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
                   "ms_per_step": fu_ms / K, "rel_err": fu_err,
                   "what": "mw_forward_inverse: forward of B maps and inverse of B independent f_lm, one recursion"},
@@ -625,6 +668,21 @@ def run_ours(args, rank, world, local_rank):
         result = {**{k: v for k, v in result.items() if k in HEAD_KEYS}, "cpu_baseline": cb,
                   **{k: v for k, v in result.items() if k not in HEAD_KEYS}}
     return result
+
+
+def headline_only_result(args, world, value, ms, K, W, L, B, stages, launches_per_step, ck, err_report, tuning):
+    """The line of a --headline-only run (for profiling: the headline round
+    trips and the per-stage breakdown, no secondary arms)."""
+    return {"metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "f64+f32+bf16", "mixed_tf32": "f64+f32+tf32"}[args.precision],
+            "data": "synthetic (seeded complex Gaussian f_lm, C_l=1/(l+1)^2)",
+            "config": {"workload": f"MW round trip (inverse then forward) L={L}, B={B} (8 maps s=0, 8 maps s=2)",
+                       "L": L, "batch": B, "precision": args.precision, "graph": True,
+                       "tuning": dict(tuning, autotuned=not (args.no_autotune or args.tuning)),
+                       "headline_only": True},
+            "gpu_launches": launches_per_step * K, "clocks": ck, "stage_ms_per_step": stages,
+            "roundtrip_rel_err": err_report["rel_max"]}
 
 
 HEAD_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
@@ -830,6 +888,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="use the fixed default tuning")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads' lines and the paper's accuracy protocol")
+    ap.add_argument("--tuning", default=None, metavar="CHUNK,GROUPS,TN_THREADS",
+                    help="apply this tuning to the headline plan instead of autotuning it")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the headline round trip and its stage breakdown (profiling runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -253,6 +253,16 @@ size_t mw_flm_size(int L);
 size_t mw_plan_workspace_bytes(const mw_plan *plan);
 int mw_plan_last_launches(const mw_plan *plan);
 
+/* 1 if the plan's length-(2L-1) DFTs (the phi DFTs of Sec. IV-D / Eq. f_pfft
+ * and the theta DFTs over the 2L-1 extended nodes, Sec. IV-C) run by
+ * Bluestein's chirp-z convolution through the smooth convolution length
+ * N >= 4L-3 (ragged plans: for at least one band limit), 0 if by the mixed-radix
+ * factorisation of 2L-1, -1 for NULL.  The plan picks the cheaper route from
+ * the factors of 2L-1 (a prime such as 4093 at L = 2047 takes Bluestein);
+ * the environment variable MW_FFT_BLUESTEIN=0 or =1, read at plan creation,
+ * forces either.  Both compute the same DFT; results differ by rounding. */
+int mw_plan_fft_bluestein(const mw_plan *plan);
+
 /* Per-stage timing (diagnostics, not in the paper).  With timing enabled, each
  * call records CUDA events on its stream around every stage:
  *   MW_STAGE_PHI     phi DFTs (and their adjoints); on real plans also the

@@ -11,7 +11,10 @@
 // overwrite the inputs, so one shared buffer of n elements suffices.  Other odd
 // primes (the 2L-1 lengths contain factors such as 13, 31, 73 or 127) use a
 // dot-product stage in which each output is an R-term sum (compensated in
-// FP32); no Bluestein step is needed.  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
+// FP32).  Where those sums would dominate (a prime 2L-1 such as 4093 makes the
+// whole FFT one 4093-term stage), the plan runs the length 2L-1 by Bluestein's
+// chirp-z convolution through a power-of-two length instead (fft_bluestein,
+// at the end).  Twiddles come from one table of e^{-2 pi i k / n}, k < n.
 #pragma once
 #include <cuda_runtime.h>
 #include "internal.h"
@@ -337,3 +340,90 @@ __device__ typename cplx<T>::t* fft_pp(typename cplx<T>::t* x, typename cplx<T>:
 
 constexpr int kFftVPT = 16;          // outputs per thread per stage (in-place variant)
 constexpr int kFftMaxThreads = 512;  // kFftVPT * kFftMaxThreads >= largest FFT (8192)
+
+// In-place FFT of a power-of-two length (radices 8, 4 and 2 only: a short
+// instantiation for the Bluestein convolution below); each thread holds VPT
+// values per stage.  Needs blockDim.x * VPT >= d.n.
+template <typename T, int VPT>
+__device__ void fft_inplace_pow2(typename cplx<T>::t* buf, const FftDesc& d, const typename cplx<T>::t* __restrict__ tw,
+                                 bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < d.nrad; ++s) {
+    const int R = d.rad[s];
+    if (R == 8) fftk::stage_reg<T, 8, VPT>(buf, d.n, Ns, tw, inv);
+    else if (R == 4) fftk::stage_reg<T, 4, VPT>(buf, d.n, Ns, tw, inv);
+    else fftk::stage_reg<T, 2, VPT>(buf, d.n, Ns, tw, inv);
+    Ns *= R;
+  }
+}
+
+// Kernels whose only large FFT is a Bluestein one run 1024-thread blocks with
+// 8 values per thread (the butterflies stay in 64 registers); kernels that
+// also hold other FFTs keep 512 threads and 16 values.
+constexpr int kBsVPT = 8;
+constexpr int kBsMaxThreads = 1024;
+
+// Bluestein's chirp-z form of a DFT of any length M.  With c_n = e^{-i pi n^2 / M},
+// nk = (n^2 + k^2 - (k - n)^2) / 2 turns the DFT into
+//   X_k = c_k sum_{n<M} (x_n c_n) conj(c_{k-n}),
+// a convolution with lags in (-M, M), exact as a circular convolution of any
+// length NB >= 2M - 1 (here a power of two).  It runs in place over
+// buf[0, NB) (NB = fB.n): x_n c_n zero-padded to NB, FFT_NB, times chirpF (the
+// DFT of conj(c) placed circularly, pre-scaled by 1/NB), inverse FFT_NB, times
+// c_k.  Input and output in buf[0, M).  The inverse DFT (e^{+}) is the
+// conjugate of the forward DFT of the conjugate.  Needs blockDim.x * VPT
+// >= NB; every thread of the block calls it, after the input is in place and
+// visible.
+template <typename T, int VPT>
+__device__ void fft_bluestein(typename cplx<T>::t* buf, int M, const FftDesc& fB,
+                              const typename cplx<T>::t* __restrict__ twB,
+                              const typename cplx<T>::t* __restrict__ chirp,
+                              const typename cplx<T>::t* __restrict__ chirpF, bool inv) {
+  using CT = typename cplx<T>::t;
+  const int NB = fB.n;
+  for (int n = threadIdx.x; n < NB; n += blockDim.x) {
+    CT v = mkc<T>(0, 0);
+    if (n < M) {
+      v = buf[n];
+      if (inv) v.y = -v.y;
+      v = fftk::mul<T>(v, chirp[n]);
+    }
+    buf[n] = v;
+  }
+  __syncthreads();
+  fft_inplace_pow2<T, VPT>(buf, fB, twB, false);
+  for (int k = threadIdx.x; k < NB; k += blockDim.x) buf[k] = fftk::mul<T>(buf[k], chirpF[k]);
+  __syncthreads();
+  fft_inplace_pow2<T, VPT>(buf, fB, twB, true);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    CT v = fftk::mul<T>(buf[k], chirp[k]);
+    if (inv) v.y = -v.y;
+    buf[k] = v;
+  }
+  __syncthreads();
+}
+
+// The length-M FFT of the MW stages (M = 2L - 1): tables of both routes.
+template <typename T>
+struct FftM {
+  FftDesc d;                                 // mixed-radix factorisation of M
+  const typename cplx<T>::t* tw;             // e^{-2 pi i k / M}, k < M
+  FftDesc dB;                                // Bluestein: the power of two NB >= 2M - 1
+  const typename cplx<T>::t* twB;            // e^{-2 pi i k / NB}, k < NB
+  const typename cplx<T>::t* chirp;          // e^{-i pi n^2 / M}, n < M
+  const typename cplx<T>::t* chirpF;         // DFT_NB of conj(chirp), circular, / NB
+};
+
+// DFT of length M of x[0, M): mixed radix with y[0, M) as the ping-pong
+// partner (BS = false; returns x or y), or Bluestein in place over x[0, NB)
+// with VPT values per thread (BS = true; returns x).
+template <typename T, bool BS, int VPT = kBsVPT>
+__device__ __forceinline__ typename cplx<T>::t* fft_m(typename cplx<T>::t* x, typename cplx<T>::t* y,
+                                                      const FftM<T>& f, bool inv) {
+  if constexpr (BS) {
+    fft_bluestein<T, VPT>(x, f.d.n, f.dB, f.twB, f.chirp, f.chirpF, inv);
+    return x;
+  } else {
+    return fft_pp<T>(x, y, f.d, f.tw, inv);
+  }
+}

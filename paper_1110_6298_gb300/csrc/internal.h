@@ -70,6 +70,14 @@ struct mw_plan {
   void* d_twN = nullptr;           // e^{-2 pi i k / N}, k < N
   void* d_phase = nullptr;         // e^{-i pi m' / M}, m' = -(L-1)..L-1 (index m'+L-1)
   void* d_V = nullptr;             // DFT_N of the reflected weights, pre-scaled by 1/(N M)
+  // length-M FFTs by Bluestein's chirp-z convolution of power-of-two length
+  // NB = fB.n >= 2M - 1 when M's prime factors would make the mixed-radix
+  // dot-product stages dearer
+  bool bluestein = false;
+  FftDesc fB{};
+  void* d_twB = nullptr;           // e^{-2 pi i k / NB}, k < NB
+  void* d_chirp = nullptr;         // e^{-i pi n^2 / M}, n < M
+  void* d_chirpF = nullptr;        // DFT_NB of conj(chirp) placed circularly, pre-scaled by 1/NB
   double* d_sqrt = nullptr;        // sqrt(k), k = 0..2L+2
   double* d_rsqrt = nullptr;       // 1/sqrt(k), k = 1..2L+2 (entry 0 unused, 0)
   double2* d_upole = nullptr;      // u(m') + u(-m') (m' > 0), u(0): pole row of the forward adjoint
@@ -130,6 +138,10 @@ struct mw_plan {
   std::vector<GraphEntry> graphs;
   bool graph_failed = false;       // capture unsupported here: run calls directly
   cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
+  // calls on pinned host buffers: the stream of the overlapped host copies
+  // and the events that order them against the compute stream
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_ev;
 
   // optional per-stage timing (CUDA events on the call's stream)
   bool timing = false;
@@ -151,10 +163,11 @@ struct StageSpan {
 };
 
 // ---- kernels (launch helpers return cudaGetLastError()) ----
-cudaError_t launch_phi_forward(const mw_plan* p, const double2* map, cudaStream_t st);
-cudaError_t launch_theta_forward(const mw_plan* p, cudaStream_t st);
-cudaError_t launch_theta_inverse(const mw_plan* p, cudaStream_t st);
-cudaError_t launch_phi_inverse(const mw_plan* p, double2* map, cudaStream_t st);
+// FFT stages of the maps [b0, b0 + nb) (nb < 0: every map of the plan)
+cudaError_t launch_phi_forward(const mw_plan* p, const double2* map, cudaStream_t st, int b0 = 0, int nb = -1);
+cudaError_t launch_theta_forward(const mw_plan* p, cudaStream_t st, int b0 = 0, int nb = -1);
+cudaError_t launch_theta_inverse(const mw_plan* p, cudaStream_t st, int b0 = 0, int nb = -1);
+cudaError_t launch_phi_inverse(const mw_plan* p, double2* map, cudaStream_t st, int b0 = 0, int nb = -1);
 cudaError_t launch_phi_forward_adjoint(const mw_plan* p, double2* map, cudaStream_t st);
 cudaError_t launch_theta_forward_adjoint(const mw_plan* p, cudaStream_t st);
 cudaError_t launch_theta_inverse_adjoint(const mw_plan* p, cudaStream_t st);
@@ -199,4 +212,12 @@ struct WignerJob {
   const double2* flm_in;
   double2* flm_out;
 };
-cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches);
+// hook: if given, called after the contraction launches of every chunk of
+// planes [l0, l1) have been enqueued on st (the forward's f_lm rows l0..l1-1
+// are then final once st reaches that point).
+struct ChunkHook {
+  cudaError_t (*fn)(void* ctx, int l0, int l1);
+  void* ctx;
+};
+cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches,
+                       const ChunkHook* hook = nullptr);

@@ -508,7 +508,8 @@ cudaError_t launch_risbo(mw_plan* p, void* S, int nslot, float* S32, int l0, int
 // ragged plan one per band-limit sub-plan; for a fused forward+inverse call
 // the forward jobs and the inverse jobs together.  Plane l serves every job
 // with L > l: Delta^l depends on neither L nor s.
-cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {
+cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches,
+                      const ChunkHook* hook) {
   const bool fp64 = o->prec == MW_PREC_FP64;
   const int chunk = fp64 ? kChunk : o->chunk;
   for (int c = 0; c < nj; ++c) {  // work lists built for another chunk (after a tuning change)
@@ -567,6 +568,10 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     }
     span_c.end(ncl);
     nl += ncl;
+    if (hook) {
+      e = hook->fn(hook->ctx, l0, l1);
+      if (e != cudaSuccess) return e;
+    }
   }
   if (launches) *launches += nl;
   return cudaGetLastError();
@@ -634,6 +639,7 @@ cudaError_t make_risbo_perm(mw_plan* p) {
   return e;
 }
 
-cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches) {
-  return run_sweep(o, jobs, nj, st, launches);
+cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches,
+                       const ChunkHook* hook) {
+  return run_sweep(o, jobs, nj, st, launches, hook);
 }

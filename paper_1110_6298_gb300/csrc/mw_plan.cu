@@ -45,6 +45,33 @@ bool smooth7(int n) {
   return n == 1;
 }
 
+// Work of one length-n FFT by the stages of fft.cuh, in complex multiply-adds
+// per element summed over the stages: about (R + 1) / 2 for a register
+// butterfly of radix R; R for a dot-product stage, weighted by 2 in single
+// precision (compensated sums) and 1.5 in double (two shared-memory loads per
+// term against one per R terms).
+double fft_work(const FftDesc& d, bool single) {
+  double c = 0.0;
+  for (int i = 0; i < d.nrad; ++i) {
+    const int R = d.rad[i];
+    const bool reg = R == 2 || R == 3 || R == 4 || R == 5 || R == 7 || R == 8 || (single && (R == 11 || R == 13));
+    c += (double)d.n * (reg ? 0.5 * (R + 1) : (single ? 2.0 : 1.5) * R);
+  }
+  return c;
+}
+
+// Whether the plan runs its length-M FFTs by Bluestein's convolution through
+// the power of two fB.n >= 2M - 1 (two FFTs of that length and three
+// pointwise products) instead of M's own radices: the cheaper by fft_work.
+// MW_FFT_BLUESTEIN=0 or =1 forces either route for every M.
+bool choose_bluestein(const FftDesc& fM, const FftDesc& fB, bool single) {
+  if (const char* v = getenv("MW_FFT_BLUESTEIN")) {
+    if (v[0] == '0') return false;
+    if (v[0] == '1') return true;
+  }
+  return 2.0 * fft_work(fB, single) + 3.0 * fB.n < fft_work(fM, single);
+}
+
 // weight w(k) of Sec. IV-D
 void weight(int k, double* re, double* im) {
   *re = 0.0;
@@ -77,11 +104,14 @@ void free_plan(mw_plan* p) {
                   p->d_map_stage2, p->d_flm_stage2,
                   p->d_prog,   p->d_rscale, p->d_nl, p->d_flmf, p->d_moff, p->d_foff, p->d_perm,
                   p->d_qw,     p->d_qpart, p->d_gpack, p->d_sqrt_ff, p->d_rsqrt_ff, p->d_rscale_ff,
-                  p->d_tn_top, p->d_tn_exp, p->d_flmT, p->d_tc2_items, p->d_twE, p->d_Ue, p->d_Uo};
+                  p->d_tn_top, p->d_tn_exp, p->d_flmT, p->d_tc2_items, p->d_twE, p->d_Ue, p->d_Uo,
+                  p->d_chirp, p->d_chirpF, p->d_twB};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (auto ev : p->copy_ev) cudaEventDestroy(ev);
   for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto ev : p->pool) cudaEventDestroy(ev);
   delete p;
@@ -223,6 +253,38 @@ mw_status build_plan(mw_plan** out, int L, int B, const int* spins, unsigned fla
   chk(dbl ? upload_complex<double>(re, im, &p->d_twM) : upload_complex<float>(re, im, &p->d_twM));
   twiddles(N);
   chk(dbl ? upload_complex<double>(re, im, &p->d_twN) : upload_complex<float>(re, im, &p->d_twN));
+  // Bluestein tables: c_n = e^{-i pi n^2 / M} = e^{-2 pi i (n^2 mod 2M) / (2M)},
+  // and the DFT of b_j = conj(c_|j|), |j| < M, placed circularly in length NB:
+  // b is even in j, so DFT_NB(b)_k = b_0 + 2 sum_{j=1}^{M-1} b_j cos(2 pi j k / NB)
+  {
+    int NB = 1;
+    while (NB < 2 * M - 1) NB *= 2;
+    factorize(NB, &p->fB);
+  }
+  p->bluestein = choose_bluestein(p->fM, p->fB, !dbl);
+  if (p->bluestein) {
+    const int NB = p->fB.n;
+    std::vector<double> cr(M), ci(M);
+    for (int n = 0; n < M; ++n) unit_root(((long long)n * n) % (2LL * M), 2LL * M, &cr[n], &ci[n]);
+    chk(dbl ? upload_complex<double>(cr, ci, &p->d_chirp) : upload_complex<float>(cr, ci, &p->d_chirp));
+    twiddles(NB);
+    chk(dbl ? upload_complex<double>(re, im, &p->d_twB) : upload_complex<float>(re, im, &p->d_twB));
+    std::vector<double> cosB(re);  // cos(2 pi x / NB)
+    re.assign(NB, 0.0); im.assign(NB, 0.0);
+    for (int k = 0; k < NB; ++k) {
+      double sr = cr[0], si = -ci[0];
+      long long x = 0;
+      for (int j = 1; j < M; ++j) {
+        x += k;
+        if (x >= NB) x -= NB;
+        sr += 2.0 * cr[j] * cosB[x];
+        si -= 2.0 * ci[j] * cosB[x];
+      }
+      re[k] = sr / NB;
+      im[k] = si / NB;
+    }
+    chk(dbl ? upload_complex<double>(re, im, &p->d_chirpF) : upload_complex<float>(re, im, &p->d_chirpF));
+  }
   // e^{-i pi m' / M} = e^{-2 pi i m' / (2M)}
   re.assign(M, 0.0); im.assign(M, 0.0);
   for (int i = 0; i < M; ++i) unit_root(i - (L - 1), 2LL * M, &re[i], &im[i]);
@@ -443,6 +505,148 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// page-locked host memory (cudaMallocHost / cudaHostRegister): copies from and
+// to it run asynchronously, so they can overlap kernels
+bool is_pinned_host_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// FFT stages of every map of a plan (the launchers also take a map range)
+cudaError_t phi_forward_all(const mw_plan* c, const double2* m, cudaStream_t st) { return launch_phi_forward(c, m, st); }
+cudaError_t phi_inverse_all(const mw_plan* c, double2* m, cudaStream_t st) { return launch_phi_inverse(c, m, st); }
+cudaError_t theta_forward_all(const mw_plan* c, cudaStream_t st) { return launch_theta_forward(c, st); }
+cudaError_t theta_inverse_all(const mw_plan* c, cudaStream_t st) { return launch_theta_inverse(c, st); }
+
+// Forward or inverse of a uniform complex plan with a pinned host input and/or
+// output: the host copies run on the plan's copy stream in pieces that
+// overlap the compute on st.
+//   forward: the maps are copied in groups; the phi and theta stages of a
+//            group start as soon as its copy has landed, while the next
+//            group's copy runs; the f_lm rows of a chunk of planes are
+//            copied back as soon as that chunk's contraction has written them.
+//   inverse: f_lm is copied in whole (the contraction reads every l of every
+//            map from the start); the theta and phi stages run group by
+//            group and each group's maps are copied back while the next
+//            group computes.
+// Device-side inputs or outputs skip their copies.  Returns after the host
+// output is written (st synchronised), as the staged path does.
+struct PinnedCopies {
+  mw_plan* p;
+  cudaStream_t st, cp;
+  double2* flm_host;   // forward: host f_lm (null: device output)
+  const double2* flm_dev;
+  int next_ev;
+};
+
+cudaError_t next_event(mw_plan* p, int* k, cudaEvent_t* ev) {
+  if (*k >= (int)p->copy_ev.size()) {
+    cudaEvent_t e;
+    const cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return r;
+    p->copy_ev.push_back(e);
+  }
+  *ev = p->copy_ev[(*k)++];
+  return cudaSuccess;
+}
+
+// st -> cp ordering: cp waits for the work enqueued on st so far
+cudaError_t order(mw_plan* p, int* k, cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t ev;
+  cudaError_t e = next_event(p, k, &ev);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, from);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+  return e;
+}
+
+cudaError_t copy_flm_rows(void* ctx, int l0, int l1) {
+  PinnedCopies* c = static_cast<PinnedCopies*>(ctx);
+  mw_plan* p = c->p;
+  if (l1 > p->L) l1 = p->L;
+  cudaError_t e = order(p, &c->next_ev, c->st, c->cp);
+  if (e != cudaSuccess) return e;
+  const size_t pitch = sizeof(double2) * (size_t)p->L * p->L;
+  const size_t off = (size_t)l0 * l0, width = sizeof(double2) * ((size_t)l1 * l1 - off);
+  return cudaMemcpy2DAsync(c->flm_host + off, pitch, c->flm_dev + off, pitch, width, p->B, cudaMemcpyDeviceToHost,
+                           c->cp);
+}
+
+cudaError_t run_pinned(mw_plan* p, bool forward, const void* in, void* out, bool in_dev, bool out_dev,
+                       const double2* din, double2* dout, cudaStream_t st, int* nl) {
+  cudaError_t e = cudaSuccess;
+  if (!p->copy_stream) {
+    e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaStream_t cp = p->copy_stream;
+  int k = 0;
+  const int B = p->B;
+  const int gm = B <= 8 ? 1 : (B + 7) / 8;  // maps per group: at most 8 groups
+  const size_t map_b = sizeof(double2) * (size_t)((long long)(p->L - 1) * p->M + 1);
+  std::vector<mw_plan*> cs{p};
+  if ((e = order(p, &k, st, cp)) != cudaSuccess) return e;  // the copies follow earlier work on st
+  if (forward) {
+    for (int b0 = 0; b0 < B && e == cudaSuccess; b0 += gm) {
+      const int nb = b0 + gm <= B ? gm : B - b0;
+      if (!in_dev) {
+        e = cudaMemcpyAsync((double2*)din + p->moff[b0], (const double2*)in + p->moff[b0], map_b * nb,
+                            cudaMemcpyHostToDevice, cp);
+        if (e == cudaSuccess) e = order(p, &k, cp, st);
+        if (e != cudaSuccess) break;
+      }
+      {
+        StageSpan sp(p, MW_STAGE_PHI, st);
+        e = launch_phi_forward(p, din, st, b0, nb);
+        sp.end(1);
+      }
+      if (e == cudaSuccess) {
+        StageSpan sp(p, MW_STAGE_THETA, st);
+        e = launch_theta_forward(p, st, b0, nb);
+        sp.end(1);
+      }
+      *nl += 2;
+    }
+    if (e != cudaSuccess) return e;
+    WignerJob job{p, 0, nullptr, dout};
+    PinnedCopies pc{p, st, cp, out_dev ? nullptr : (double2*)out, dout, k};
+    ChunkHook hook{copy_flm_rows, &pc};
+    e = run_wigner(p, &job, 1, st, nl, out_dev ? nullptr : &hook);
+    k = pc.next_ev;
+  } else {
+    if (!in_dev) e = cudaMemcpyAsync((double2*)din, in, sizeof(double2) * (size_t)p->flm_elems,
+                                     cudaMemcpyHostToDevice, st);
+    WignerJob job{p, 1, din, nullptr};
+    if (e == cudaSuccess) e = run_wigner(p, &job, 1, st, nl);
+    for (int b0 = 0; b0 < B && e == cudaSuccess; b0 += gm) {
+      const int nb = b0 + gm <= B ? gm : B - b0;
+      {
+        StageSpan sp(p, MW_STAGE_THETA, st);
+        e = launch_theta_inverse(p, st, b0, nb);
+        sp.end(1);
+      }
+      if (e == cudaSuccess) {
+        StageSpan sp(p, MW_STAGE_PHI, st);
+        e = launch_phi_inverse(p, dout, st, b0, nb);
+        sp.end(1);
+      }
+      *nl += 2;
+      if (e == cudaSuccess && !out_dev) {
+        e = order(p, &k, st, cp);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync((double2*)out + p->moff[b0], dout + p->moff[b0], map_b * nb, cudaMemcpyDeviceToHost,
+                              cp);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = order(p, &k, cp, st);  // st resumes after the last copy
+  if (e == cudaSuccess && !out_dev) e = cudaStreamSynchronize(st);
+  return e;
+}
+
 enum Direction { kForward, kInverse, kForwardAdjoint, kInverseAdjoint, kFused };
 
 // Twins for fused forward+inverse calls: one per consumer plan (the plan
@@ -524,6 +728,15 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   if (!in2_dev) ensure(&p->d_flm_stage2, nlm);
   if (!out2_dev) ensure(&p->d_map_stage2, nmw);
   if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e); }
+  // pinned host buffers of a uniform complex plan: overlapped copies
+  if (!fused && !real && p->subs.empty() && (dir == kForward || dir == kInverse) && (!in_dev || !out_dev) &&
+      (in_dev || is_pinned_host_ptr(in)) && (out_dev || is_pinned_host_ptr(out))) {
+    int nl = 0;
+    e = run_pinned(p, dir == kForward, in, out, in_dev, out_dev, in_dev ? din : *in_slot, out_dev ? dout : *out_slot,
+                   st, &nl);
+    p->last_launches = nl;
+    return from_cuda(e);
+  }
   if (!in_dev) {
     e = cudaMemcpyAsync(*in_slot, in, in_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
@@ -587,24 +800,24 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
     switch (dir) {
       case kForward:
         phi(cs, launch_phi_forward_real, (const double*)din);
-        stage(cs, MW_STAGE_THETA, launch_theta_forward);
+        stage(cs, MW_STAGE_THETA, theta_forward_all);
         wigner(cs, c->d_gpack, none, nullptr);
         unpack(c, dout);
         break;
       case kInverse:
         pack(c, din);
         wigner(none, nullptr, cs, c->d_gpack);
-        stage(cs, MW_STAGE_THETA, launch_theta_inverse);
+        stage(cs, MW_STAGE_THETA, theta_inverse_all);
         phi(cs, launch_phi_inverse_real, (double*)dout);
         break;
       case kFused: {
         mw_plan* t = p->twins[0];
         phi(cs, launch_phi_forward_real, (const double*)din);
-        stage(cs, MW_STAGE_THETA, launch_theta_forward);
+        stage(cs, MW_STAGE_THETA, theta_forward_all);
         pack(t, din2);
         wigner(cs, c->d_gpack, p->twins, t->d_gpack);
         unpack(c, dout);
-        stage(p->twins, MW_STAGE_THETA, launch_theta_inverse);
+        stage(p->twins, MW_STAGE_THETA, theta_inverse_all);
         phi(p->twins, launch_phi_inverse_real, (double*)dout2);
         break;
       }
@@ -615,14 +828,14 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
   }
   switch (dir) {
     case kForward:
-      phi(cs, launch_phi_forward, din);
-      stage(cs, MW_STAGE_THETA, launch_theta_forward);
+      phi(cs, phi_forward_all, din);
+      stage(cs, MW_STAGE_THETA, theta_forward_all);
       wigner(cs, dout, none, nullptr);
       break;
     case kInverse:
       wigner(none, nullptr, cs, din);
-      stage(cs, MW_STAGE_THETA, launch_theta_inverse);
-      phi(cs, launch_phi_inverse, dout);
+      stage(cs, MW_STAGE_THETA, theta_inverse_all);
+      phi(cs, phi_inverse_all, dout);
       break;
     case kForwardAdjoint:
       wigner(none, nullptr, cs, din);
@@ -636,11 +849,11 @@ mw_status run(mw_plan* p, Direction dir, const void* in, void* out, void* stream
       wigner(cs, dout, none, nullptr);
       break;
     case kFused:  // forward half on cs, inverse half on the twins, one sweep for both
-      phi(cs, launch_phi_forward, din);
-      stage(cs, MW_STAGE_THETA, launch_theta_forward);
+      phi(cs, phi_forward_all, din);
+      stage(cs, MW_STAGE_THETA, theta_forward_all);
       wigner(cs, dout, p->twins, din2);
-      stage(p->twins, MW_STAGE_THETA, launch_theta_inverse);
-      phi(p->twins, launch_phi_inverse, dout2);
+      stage(p->twins, MW_STAGE_THETA, theta_inverse_all);
+      phi(p->twins, phi_inverse_all, dout2);
       break;
   }
   return e;
@@ -1141,5 +1354,12 @@ size_t mw_map_size(int L) { return L < 1 ? 0 : (size_t)(L - 1) * (2 * (size_t)L 
 size_t mw_flm_size(int L) { return L < 1 ? 0 : (size_t)L * (size_t)L; }
 size_t mw_plan_workspace_bytes(const mw_plan* plan) { return plan ? plan->ws_bytes : 0; }
 int mw_plan_last_launches(const mw_plan* plan) { return plan ? plan->last_launches : 0; }
+int mw_plan_fft_bluestein(const mw_plan* plan) {
+  if (!plan) return -1;
+  if (plan->bluestein) return 1;
+  for (const mw_plan* c : plan->subs)
+    if (c->bluestein) return 1;
+  return 0;
+}
 
 }  // extern "C"

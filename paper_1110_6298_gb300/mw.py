@@ -78,6 +78,8 @@ def lib():
         L.mw_plan_workspace_bytes.restype = c_size
         L.mw_plan_last_launches.argtypes = [vp]
         L.mw_plan_last_launches.restype = c_int
+        L.mw_plan_fft_bluestein.argtypes = [vp]
+        L.mw_plan_fft_bluestein.restype = c_int
         L.mw_plan_sync.argtypes = [vp, vp]
         L.mw_plan_sync.restype = c_int
         L.mw_plan_set_timing.argtypes = [vp, c_int]
@@ -272,6 +274,11 @@ class Plan:
     @property
     def last_launches(self):
         return int(lib().mw_plan_last_launches(self._h))
+
+    @property
+    def fft_bluestein(self):
+        """True if the length-(2L-1) DFTs run by Bluestein's convolution."""
+        return bool(lib().mw_plan_fft_bluestein(self._h) == 1)
 
     def sync(self, stream=None):
         """Wait for this plan's work and raise MWError on a device-side timeout."""
