@@ -37,10 +37,19 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# stage kernels, keyed by (L, B, precision), from a 1-pass ncu capture of this
-# bench's round trip with the kernels as they are now (the capture command is
-# given beside the figures in profiles/); a stage absent here reports null.
-TRAFFIC = {}
+# stage kernels in one round trip (inverse launches first), keyed by (L, B,
+# precision, planes per launch, spin groups per contraction pass), from a
+# 1-pass ncu capture of the headline round trip (bench.py --headline-only
+# --tuning 512,1,128) with the kernels as they are now; a stage or tuning
+# absent here reports null.
+TRAFFIC = {
+    (2048, 16, "mixed", 512, 1): {
+        "contract": [0.509e9, 3.029e9, 7.482e9, 13.976e9, 0.452e9, 2.409e9, 6.017e9, 11.443e9],
+        "delta": [0.125e9, 1.218e9, 3.383e9, 6.621e9, 0.125e9, 1.218e9, 3.383e9, 6.622e9],
+        "theta": [3.193e9, 2.101e9],
+        "phi": [3.156e9, 3.205e9],
+    },
+}
 
 
 def peaks():
@@ -609,7 +618,7 @@ def run_ours(args, rank, world, local_rank):
         rb_line["delta_roofline"] = delta_roofline("risbo_ff", L, rb_line["stage_ms_per_step"]["delta"] / 1e3, pk,
                                                    fp32_issue, n_sm, mhz)
     dom = max(("delta", "contract", "theta", "phi"), key=lambda k: stages[k])
-    traffic = TRAFFIC.get((L, B, args.precision)) if recursion == "tn" else None
+    traffic = TRAFFIC.get((L, B, args.precision, tuning["chunk"], tuning["groups"])) if recursion == "tn" else None
     for k, v in (traffic or {}).items():
         if k in stage_roof and v:
             stage_roof[k]["traffic"] = sum(v) / len(v)  # DRAM bytes per launch, averaged over the launches
