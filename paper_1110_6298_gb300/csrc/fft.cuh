@@ -338,6 +338,64 @@ __device__ typename cplx<T>::t* fft_pp(typename cplx<T>::t* x, typename cplx<T>:
   return x;
 }
 
+// Two sequences of the same length at once: the second at x + off (its
+// ping-pong partner at y + off).  Each stage runs the butterflies of both
+// sequences between one pair of barriers.  Returns the buffer holding the
+// first result (the second is at the same place + off).
+namespace fftk {
+template <typename T, int R>
+__device__ __forceinline__ void stage_pp2(const C<T>* __restrict__ in, C<T>* __restrict__ out, int n, int off, int Ns,
+                                          const C<T>* __restrict__ tw, bool inv) {
+  const int nb = n / R, step = n / (Ns * R);
+  for (int jj = threadIdx.x; jj < 2 * nb; jj += blockDim.x) {
+    const int sq = jj >= nb ? 1 : 0, j = jj - sq * nb;
+    const C<T>* src = in + sq * off;
+    C<T> v[R];
+    const int jm = j % Ns;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C<T> w = tw[(r * jm) * step];
+        v[r] = inv ? mulc<T>(v[r], w) : mul<T>(v[r], w);
+      }
+    }
+    dft_small<T, R>(v, inv);
+    C<T>* dst = out + sq * off + (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+}  // namespace fftk
+
+template <typename T>
+__device__ typename cplx<T>::t* fft_pp2(typename cplx<T>::t* x, typename cplx<T>::t* y, int off, const FftDesc& d,
+                                        const typename cplx<T>::t* __restrict__ tw, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < d.nrad; ++s) {
+    const int R = d.rad[s];
+    switch (R) {
+      case 2: fftk::stage_pp2<T, 2>(x, y, d.n, off, Ns, tw, inv); break;
+      case 3: fftk::stage_pp2<T, 3>(x, y, d.n, off, Ns, tw, inv); break;
+      case 4: fftk::stage_pp2<T, 4>(x, y, d.n, off, Ns, tw, inv); break;
+      case 5: fftk::stage_pp2<T, 5>(x, y, d.n, off, Ns, tw, inv); break;
+      case 7: fftk::stage_pp2<T, 7>(x, y, d.n, off, Ns, tw, inv); break;
+      case 8: fftk::stage_pp2<T, 8>(x, y, d.n, off, Ns, tw, inv); break;
+      default:  // other radices: one sequence after the other
+        fftk::stage_dot_pp<T>(x, y, d.n, Ns, R, tw, inv);
+        fftk::stage_dot_pp<T>(x + off, y + off, d.n, Ns, R, tw, inv);
+        break;
+    }
+    typename cplx<T>::t* t = x;
+    x = y;
+    y = t;
+    Ns *= R;
+  }
+  return x;
+}
+
 constexpr int kFftVPT = 16;          // outputs per thread per stage (in-place variant)
 constexpr int kFftMaxThreads = 512;  // kFftVPT * kFftMaxThreads >= largest FFT (8192)
 

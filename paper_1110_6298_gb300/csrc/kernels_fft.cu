@@ -135,15 +135,16 @@ __device__ __forceinline__ void theta_forward_even_body(
     }
   }
   __syncthreads();
-  C<T>* xe = fft_pp<T>(X, X + NE, fE, twE, true);
-  C<T>* xo = fft_pp<T>(Y, Y + NE, fE, twE, true);
+  // both halves in one pass per FFT stage (Y = X + 2 NE)
+  C<T>* xe = fft_pp2<T>(X, X + NE, 2 * NE, fE, twE, true);
+  C<T>* xo = xe + 2 * NE;
   for (int k = threadIdx.x; k < NE; k += blockDim.x) {
     xe[k] = cmul<T>(xe[k], Ue[k]);
     xo[k] = cmul<T>(xo[k], Uo[k]);
   }
   __syncthreads();
-  xe = fft_pp<T>(xe, xe == X ? X + NE : X, fE, twE, false);
-  xo = fft_pp<T>(xo, xo == Y ? Y + NE : Y, fE, twE, false);
+  xe = fft_pp2<T>(xe, xe == X ? X + NE : X, 2 * NE, fE, twE, false);
+  xo = xe + 2 * NE;
   // G+_{m,0} = G_m0, G+_{m,m'} = 2 G_mm' (m' > 0): m' = 2i from the even half, 2i+1 from the odd
   C<T>* out = Gp + ((long long)b * M + im) * L;
   for (int mp = threadIdx.x; mp < L; mp += blockDim.x) {

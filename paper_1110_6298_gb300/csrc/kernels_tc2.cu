@@ -30,7 +30,7 @@
 //                  (cp.async.bulk.tensor, this GPU's memory only, no
 //                  multicast) four K tiles ahead, and issues the MMAs of the
 //                  next K tile before its warp drains the current one.
-// Operands and accumulators are double-buffered; stages are handed over with
+// Operands and their accumulators run in kS = 2 stages; stages are handed over with
 // mbarriers: TMA bytes -> producers -> MMA -> (producers, drain) -> MMA.  A
 // waiting thread is suspended in mbarrier.try_wait rather than spinning.
 // Every wait is bounded (2 s of wall clock): a wait that gives up records the
@@ -62,19 +62,23 @@ constexpr uint32_t kWaitNs = 2000000000u;  // 2 s: a healthy wait ends within mi
 template <int NG>
 struct Layout {
   static constexpr int kTS = NG == 2 ? 3 : 4;                        // TMA stages (plane tiles in flight)
+  // operand + accumulator stages (A in TMEM, B in smem, the accumulators they
+  // feed); 3 or 4 fit the TMEM with one spin group per pass but measured no
+  // faster at L = 2048 (31.0 ms per round trip with 2, 3 or 4 stages)
+  static constexpr int kS = 2;
   static constexpr int kTmaStage = (1 + NG) * kTmaTile;             // row am + one spin row per group
   static constexpr int kBStage = NG * 3 * kBTile;
   static constexpr int kTmaOff = 0;                                  // 1024-aligned
   static constexpr int kBOff = kTS * kTmaStage;
-  static constexpr int kEpiOff = kBOff + 2 * kBStage;               // epilogue staging of one group
+  static constexpr int kEpiOff = kBOff + kS * kBStage;              // epilogue staging of one group
   static constexpr int kEpiBytes = 32 * 256 * 4;                     // 32 values x 256 drain threads
   static constexpr int kBarOff = kEpiOff + kEpiBytes;
-  static constexpr int kBytes = kBarOff + 192;
+  static constexpr int kBytes = kBarOff + 256;
   static constexpr int kSmem = kBytes + 1024;                        // slack for the manual alignment
-  // TMEM columns: accumulators (hi, corr) per buffer and group, then A per
+  // TMEM columns: accumulators (hi, corr) per stage and group, then A per
   // stage, group, K step and split (8 columns = 16 bf16 of K each)
-  static constexpr int kAccCols = 2 * NG * 64;
-  static constexpr int kCols = kAccCols + 2 * NG * 2 * 3 * 8;
+  static constexpr int kAccCols = kS * NG * 64;
+  static constexpr int kCols = kAccCols + kS * NG * 2 * 3 * 8;
   static constexpr uint32_t kAlloc = kCols <= 256 ? 256u : 512u;
   static_assert(kCols <= 512, "TMEM budget");
   static_assert(kSmem <= 227 * 1024, "shared memory budget");
@@ -225,18 +229,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
   const uint32_t raw = umma::smem_u32(smem_raw);
   unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Ly::kBarOff);
-  uint64_t* tma_full = bar;             // [kTS] TMA bytes of a plane-tile stage arrived
-  uint64_t* full = bar + kTS;           // [2] producers wrote A (TMEM) and B (smem) of an operand stage
-  uint64_t* done = bar + kTS + 2;       // [2] the MMAs of an operand stage completed
-  uint64_t* accempty = bar + kTS + 4;   // [2] the drain read an accumulator buffer
-  uint64_t* fin = bar + kTS + 6;        // final MMA completion on the abort path
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kTS + 7);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + kTS + 8);
+  constexpr int kS = Ly::kS;
+  uint64_t* tma_full = bar;                  // [kTS] TMA bytes of a plane-tile stage arrived
+  uint64_t* full = bar + kTS;                // [kS] producers wrote A (TMEM) and B (smem) of a stage
+  uint64_t* done = bar + kTS + kS;           // [kS] the MMAs of a stage completed
+  uint64_t* accempty = bar + kTS + 2 * kS;   // [kS] the drain read a stage's accumulators
+  uint64_t* fin = bar + kTS + 3 * kS;        // final MMA completion on the abort path
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kTS + 3 * kS + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + kTS + 3 * kS + 2);
+  static_assert((kTS + 3 * kS + 3) * 8 <= 256, "barrier area");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   if (tid == 0) {
     for (int t = 0; t < kTS; ++t) umma::mbar_init(&tma_full[t], 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kS; ++s) {
       umma::mbar_init(&full[s], 8);
       umma::mbar_init(&done[s], 1);
       umma::mbar_init(&accempty[s], 8);
@@ -334,11 +340,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     // plane tiles of TMA stage q % kTS into tensor memory.
     auto body = [&](float (&cur)[8], uint32_t& csg) -> bool {
       if (it >= A.nitems) return false;
-      const int s = q & 1, ts = q % kTS;
-      const uint32_t ph = (uint32_t)(q >> 1) & 1u, tph = (uint32_t)(q / kTS) & 1u;
+      const int s = q % kS, ts = q % kTS;
+      const uint32_t ph = (uint32_t)(q / kS) & 1u, tph = (uint32_t)(q / kTS) & 1u;
       // every lane waits; the outcome is made warp-uniform so that the
       // warp-collective TMEM stores and __syncwarp below never diverge
-      const bool w = (q < 2 || wait_bar(&done[s], ph ^ 1u, abort_flag)) && wait_bar(&tma_full[ts], tph, abort_flag);
+      const bool w = (q < kS || wait_bar(&done[s], ph ^ 1u, abort_flag)) && wait_bar(&tma_full[ts], tph, abort_flag);
       if (!__all_sync(0xffffffffu, w)) {
         if (lane == 0) fail();
         return false;
@@ -499,9 +505,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     // MMAs of the MMA cursor's position, then the TMA kTS positions ahead
     auto mma_step = [&]() {
       if (!cok || Qm.it >= A.nitems) return;
-      const int st = qm & 1;
-      const uint32_t ph = (uint32_t)(qm >> 1) & 1u;
-      if (!wait_bar(&full[st], ph, abort_flag) || (qm >= 2 && !wait_bar(&accempty[st], ph ^ 1u, abort_flag))) {
+      const int st = qm % kS;
+      const uint32_t ph = (uint32_t)(qm / kS) & 1u;
+      if (!wait_bar(&full[st], ph, abort_flag) || (qm >= kS && !wait_bar(&accempty[st], ph ^ 1u, abort_flag))) {
         fail();
         cok = false;
         return;
@@ -552,8 +558,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       const Item x = item_of<DIR>(A, it);
       const int ngl = min(NG, A.ng - x.gs * NG);
       for (int kt = 0; kt < x.nk; ++kt, ++q) {
-        const int s = q & 1;
-        const uint32_t ph = (uint32_t)(q >> 1) & 1u;
+        const int s = q % kS;
+        const uint32_t ph = (uint32_t)(q / kS) & 1u;
         if (warp == 8) {
           if (ctl) mma_step();  // position q + 1
           __syncwarp();
