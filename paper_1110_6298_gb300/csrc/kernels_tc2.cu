@@ -77,13 +77,20 @@ struct Layout {
   static constexpr int kSmem = kBytes + 1024;                        // slack for the manual alignment
   // TMEM columns: accumulators (hi, corr) per stage and group, then A per
   // stage, group, K step and split (8 columns = 16 bf16 of K each)
-  static constexpr int kAccCols = kS * NG * 64;
+  // hi.hi accumulator per stage and group; correction accumulator per item
+  // parity and group (it collects the five correction products of every K
+  // tile of an item and is read once, at the item's last K tile)
+  static constexpr int kAccCols = (kS + 2) * NG * 32;
   static constexpr int kCols = kAccCols + kS * NG * 2 * 3 * 8;
   static constexpr uint32_t kAlloc = kCols <= 256 ? 256u : 512u;
   static_assert(kCols <= 512, "TMEM budget");
   static_assert(kSmem <= 227 * 1024, "shared memory budget");
-  __device__ static uint32_t acc_hi(int a, int g) { return (uint32_t)((a * NG + g) * 64); }
-  __device__ static uint32_t acc_corr(int a, int g) { return (uint32_t)((a * NG + g) * 64 + 32); }
+  __device__ static uint32_t acc_hi(int a, int g) { return (uint32_t)((a * NG + g) * 32); }
+  __device__ static uint32_t acc_corr(int ip, int g) { return (uint32_t)((kS * NG + ip * NG + g) * 32); }
+  // the correction accumulator of item k is reused by item k + 2, whose first
+  // MMAs wait (accempty) for the drain of a position at least kS later than
+  // item k's last one, which reads it: needs kS <= 2
+  static_assert(kS <= 2, "item-parity correction accumulators");
   __device__ static uint32_t a_col(int s, int g, int ks, int sp) {
     return (uint32_t)(kAccCols + ((s * NG + g) * 2 + ks) * 24 + sp * 8);
   }
@@ -237,15 +244,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
   uint64_t* fin = bar + kTS + 3 * kS;        // final MMA completion on the abort path
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kTS + 3 * kS + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + kTS + 3 * kS + 2);
-  static_assert((kTS + 3 * kS + 3) * 8 <= 256, "barrier area");
+  uint64_t* tma_empty = bar + kTS + 3 * kS + 3;  // [kTS] producers read a plane-tile stage (split roles)
+  static_assert((2 * kTS + 3 * kS + 3) * 8 <= 256, "barrier area");
+  // Roles of warps 8..15.  One spin group per pass (NG = 1): lane 0 of warp 8
+  // issues the MMAs, lane 0 of warp 9 the TMA loads (refilling a stage once
+  // the producers report it read), and warps 12..15 drain all 32 accumulator
+  // columns of their lane quarter.  Two groups (NG = 2, whose float-float
+  // accumulators would not fit 4 drain warps' registers): lane 0 of warp 8
+  // does both issues between draining with the other 7 warps, each warp 16
+  // columns of its lane quarter.
+  constexpr bool kSplit = NG == 1;
+  constexpr int kCH = kSplit ? 4 : 2;        // 8-column accumulator chunks per drain thread
+  constexpr int kDT = kSplit ? 128 : 256;    // drain threads
+  constexpr int kPairs = 4 * kCH;            // (map, sign) columns per drain thread
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   if (tid == 0) {
     for (int t = 0; t < kTS; ++t) umma::mbar_init(&tma_full[t], 1);
+    for (int t = 0; t < kTS; ++t) umma::mbar_init(&tma_empty[t], 8);
     for (int s = 0; s < kS; ++s) {
       umma::mbar_init(&full[s], 8);
       umma::mbar_init(&done[s], 1);
-      umma::mbar_init(&accempty[s], 8);
+      umma::mbar_init(&accempty[s], kDT / 32);  // one arrival per drain warp
     }
     umma::mbar_init(fin, 1);
     *abort_flag = 0;
@@ -434,7 +454,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       umma::fence_proxy_async();
       umma::fence_before();
       __syncwarp();
-      if (lane == 0) arrive(&full[s]);
+      if (lane == 0) {
+        arrive(&full[s]);
+        if (kSplit) arrive(&tma_empty[ts]);  // T and W of this stage are no longer read
+      }
       ++q;
       if (++kt >= x.nk) {
         kt = 0;
@@ -447,21 +470,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     while (body(b0, sg0) && body(b1, sg1)) {
     }
   } else {
-    // --------------------------------------------------------------- drain
-    // Warps 8..15; lane 0 of warp 8 is also the control thread: it loads the
-    // FP32 plane tiles by TMA kTS positions ahead and issues the MMAs of the
-    // next position before its warp drains the current one, so the tensor
-    // core works on position q+1 while the drain warps read position q.
-    const int dw = warp - 8, half = dw >> 2, qd = warp & 3;
+    // ------------------------------------------------- control and drain
+    // NG = 2: lane 0 of warp 8 is the control thread: it loads the FP32 plane
+    // tiles by TMA kTS positions ahead and issues the MMAs of the next position
+    // before its warp drains the current one, so the tensor core works on
+    // position q+1 while the drain warps read position q.  NG = 1: the two
+    // issues run on their own lanes (warps 8 and 9) and never wait for a drain.
+    const int qd = warp & 3;
+    const int half = kSplit ? 0 : (warp - 8) >> 2;
+    const int dt = tid - (kSplit ? 12 : 8) * 32;  // drain thread index
+    const bool drainer = kSplit ? warp >= 12 : true;
     const uint32_t lane_addr = (uint32_t)(32 * qd) << 16;
-    const bool ctl = warp == 8 && lane == 0;
+    const bool ctl = warp == 8 && lane == 0;             // issues the MMAs (and, NG = 2, the TMA loads)
+    const bool tma_thr = kSplit ? (warp == 9 && lane == 0) : ctl;
     struct TmaPos {
       int it, kt, nk, am, t0, kstart;
       int asr[NG];
     } P;  // TMA cursor (kTS positions ahead of the MMA cursor)
     struct MmaPos {
-      int it, kt, nk, ngl;
-    } Qm;  // MMA cursor
+      int it, kt, nk, ngl, ip;
+    } Qm{};  // MMA cursor (ip: parity of the item among this CTA's items)
     int n_tma = 0;  // TMA loads issued (stage t took those with index % kTS == t)
     int qm = 0;  // MMA position
     bool cok = true;
@@ -493,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       if (++P.kt >= P.nk) load_pos(P.it + G);
     };
     auto load_mpos = [&](int itp) {
+      Qm.ip = itp == (int)blockIdx.x ? 0 : Qm.ip ^ 1;
       Qm.it = itp;
       Qm.kt = 0;
       if (itp >= A.nitems) return;
@@ -518,7 +547,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       // Consecutive MMAs go to different accumulators (the groups' hi and
       // correction slots), so that accumulation chains overlap in the pipe.
       const uint64_t bd_s = bdesc0 + (uint64_t)((st * Ly::kBStage) >> 4);
-      const uint32_t acc_s = tmem + Ly::acc_hi(st, 0), a_s = tmem + Ly::a_col(st, 0, 0, 0);
+      const uint32_t acc_s = tmem + Ly::acc_hi(st, 0), corr_s = tmem + Ly::acc_corr(Qm.ip, 0);
+      const uint32_t a_s = tmem + Ly::a_col(st, 0, 0, 0);
+      const bool first = Qm.kt == 0;  // the item's first K tile starts its correction accumulator
       auto issue = [&](auto ngc) {
         constexpr int NGC = decltype(ngc)::value;
 #pragma unroll
@@ -527,40 +558,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
           for (int p = 0; p < 6; ++p)
 #pragma unroll
             for (int g = 0; g < NGC; ++g)
-              mma_ta(acc_s + (uint32_t)(g * 64 + (p == 0 ? 0 : 32)),
+              mma_ta((p == 0 ? acc_s : corr_s) + (uint32_t)(g * 32),
                      a_s + (uint32_t)((g * 2 + k2) * 24 + split_a(p) * 8),
                      bd_s + (uint64_t)((((g * 3 + split_b(p)) * kBTile) + k2 * 256) >> 4), idesc,
-                     (p == 0) ? (k2 > 0) : !(k2 == 0 && p == 1));
+                     (p == 0) ? (k2 > 0) : !(first && k2 == 0 && p == 1));
       };
       if (NG == 2 && Qm.ngl == 2) issue(std::integral_constant<int, NG>{});
       else issue(std::integral_constant<int, 1>{});
       umma::commit(&done[st]);
       // the plane tiles of this position were read (full was observed): refill
-      if (P.it < A.nitems) issue_tma(qm % kTS);
+      if (!kSplit && P.it < A.nitems) issue_tma(qm % kTS);
       ++qm;
       if (++Qm.kt >= Qm.nk) load_mpos(Qm.it + G);
     };
-    if (ctl) {
+    if (tma_thr) {
       load_pos(blockIdx.x);
       for (int t = 0; t < kTS && P.it < A.nitems; ++t) issue_tma(t);
+    }
+    if (ctl) {
       load_mpos(blockIdx.x);
-      mma_step();  // position 0
+      if (kSplit) {
+        while (cok && Qm.it < A.nitems) mma_step();
+      } else {
+        mma_step();  // position 0
+      }
+    } else if (kSplit && tma_thr) {
+      // refill the stage of position qt with position qt + kTS once the
+      // producers have read it
+      for (int qt = 0; P.it < A.nitems; ++qt) {
+        const int t = qt % kTS;
+        if (!wait_bar(&tma_empty[t], (uint32_t)(qt / kTS) & 1u, abort_flag)) {
+          fail();
+          break;
+        }
+        issue_tma(t);
+      }
     }
     __syncwarp();
-    float hi[NG][16], lo[NG][16];
+    float hi[NG][8 * kCH], lo[NG][8 * kCH];
 #pragma unroll
     for (int g = 0; g < NG; ++g)
 #pragma unroll
-      for (int j = 0; j < 16; ++j) hi[g][j] = lo[g][j] = 0.f;
-    int q = 0;
-    bool ok = true;
-    for (int it = blockIdx.x; ok && it < A.nitems; it += G) {
+      for (int j = 0; j < 8 * kCH; ++j) hi[g][j] = lo[g][j] = 0.f;
+    int q = 0, ipd = 0;  // ipd: parity of the drained item
+    bool ok = drainer;
+    for (int it = blockIdx.x; ok && it < A.nitems; it += G, ipd ^= 1) {
       const Item x = item_of<DIR>(A, it);
       const int ngl = min(NG, A.ng - x.gs * NG);
       for (int kt = 0; kt < x.nk; ++kt, ++q) {
         const int s = q % kS;
         const uint32_t ph = (uint32_t)(q / kS) & 1u;
-        if (warp == 8) {
+        if (!kSplit && warp == 8) {
           if (ctl) mma_step();  // position q + 1
           __syncwarp();
         }
@@ -574,15 +622,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
         for (int g = 0; g < NG; ++g) {
           if (g >= ngl) continue;
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            uint32_t vh[8], vc[8];
+          for (int c = 0; c < kCH; ++c) {
+            uint32_t vh[8];
             tmem_ld8(tmem + lane_addr + Ly::acc_hi(s, g) + 16 * half + 8 * c, vh);
-            tmem_ld8(tmem + lane_addr + Ly::acc_corr(s, g) + 16 * half + 8 * c, vc);
             umma::wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              two_sum_acc(hi[g][8 * c + j], lo[g][8 * c + j], __uint_as_float(vh[j]));
-              lo[g][8 * c + j] = __fadd_rn(lo[g][8 * c + j], __uint_as_float(vc[j]));
+            for (int j = 0; j < 8; ++j) two_sum_acc(hi[g][8 * c + j], lo[g][8 * c + j], __uint_as_float(vh[j]));
+          }
+          if (kt + 1 == x.nk) {  // the item's correction products, once
+#pragma unroll
+            for (int c = 0; c < kCH; ++c) {
+              uint32_t vc[8];
+              tmem_ld8(tmem + lane_addr + Ly::acc_corr(ipd, g) + 16 * half + 8 * c, vc);
+              umma::wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) lo[g][8 * c + j] = __fadd_rn(lo[g][8 * c + j], __uint_as_float(vc[j]));
             }
           }
         }
@@ -595,44 +649,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
         // k * 256 + t, conflict-free) so that they are not live in registers
         // while its outputs are formed
         const int row = x.t0 + 32 * qd + lane;
-        float* epi = reinterpret_cast<float*>(smem + Ly::kEpiOff) + (tid - 8 * 32);
+        float* epi = reinterpret_cast<float*>(smem + Ly::kEpiOff) + dt;
         const volatile float* ep = epi;
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
           if (g >= ngl) continue;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            epi[j * 256] = hi[g][j];
-            epi[(16 + j) * 256] = lo[g][j];
+          for (int j = 0; j < 8 * kCH; ++j) {
+            epi[j * kDT] = hi[g][j];
+            epi[(8 * kCH + j) * kDT] = lo[g][j];
             hi[g][j] = lo[g][j] = 0.f;
           }
           // the group's map indices for this thread's 8 (map, sign) columns,
           // loaded together, then the outputs' addresses, loaded together
           const SpinGroup* sgp = A.groups + (x.gs * NG + g);
           const int sv = sgp->s, as = sv < 0 ? -sv : sv, nb = sgp->nb;
-          int mapj[8];
+          int mapj[kPairs];
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int j = 8 * half + jj;
+          for (int jj = 0; jj < kPairs; ++jj) {
+            const int j = kPairs * half + jj;
             const bool neg = j >= nb;
             mapj[jj] = (j < 2 * nb && !(neg && x.am == 0)) ? sgp->maps[neg ? j - nb : j] : -1;
           }
           if (DIR == 0) {
             const int l = row;
             if (l >= x.am && l < A.l1c) {
-              long long base[8];
+              long long base[kPairs];
 #pragma unroll
-              for (int jj = 0; jj < 8; ++jj) base[jj] = mapj[jj] >= 0 ? A.foff[mapj[jj]] : 0;
+              for (int jj = 0; jj < kPairs; ++jj) base[jj] = mapj[jj] >= 0 ? A.foff[mapj[jj]] : 0;
               const double nl = ((sv & 1) ? -1.0 : 1.0) * A.nl[l];
 #pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {
+              for (int jj = 0; jj < kPairs; ++jj) {
                 if (mapj[jj] < 0) continue;
-                const bool neg = 8 * half + jj >= nb;
+                const bool neg = kPairs * half + jj >= nb;
                 const int m = neg ? -x.am : x.am;
                 double2 o = make_double2(0.0, 0.0);
                 if (l >= as) {
-                  double ar = (double)ep[(2 * jj) * 256] + (double)ep[(16 + 2 * jj) * 256];
-                  double ai = (double)ep[(2 * jj + 1) * 256] + (double)ep[(16 + 2 * jj + 1) * 256];
+                  double ar = (double)ep[(2 * jj) * kDT] + (double)ep[(8 * kCH + 2 * jj) * kDT];
+                  double ai = (double)ep[(2 * jj + 1) * kDT] + (double)ep[(8 * kCH + 2 * jj + 1) * kDT];
                   const double sg2 = (neg && (l & 1)) ? -nl : nl;
                   ar *= sg2;
                   ai *= sg2;
@@ -650,13 +704,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
             const int mpr = row;
             if (mpr < A.L && mpr < A.l1c) {
 #pragma unroll
-              for (int j0 = 0; j0 < 8; j0 += 4) {  // four read-modify-writes in flight at a time
+              for (int j0 = 0; j0 < kPairs; j0 += 4) {  // four read-modify-writes in flight at a time
                 float4* dst[4];
                 float4 cur[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   const int jj = j0 + u;
-                  const bool neg = 8 * half + jj >= nb;
+                  const bool neg = kPairs * half + jj >= nb;
                   dst[u] = reinterpret_cast<float4*>(A.Fp) +
                            ((size_t)(mapj[jj] < 0 ? 0 : mapj[jj]) * A.M + (neg ? -x.am : x.am) + A.L - 1) * A.L + mpr;
                   cur[u] = mapj[jj] >= 0 ? *dst[u] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -665,9 +719,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
                 for (int u = 0; u < 4; ++u) {
                   const int jj = j0 + u;
                   if (mapj[jj] < 0) continue;
-                  const bool neg = 8 * half + jj >= nb;
-                  float rh = ep[(2 * jj) * 256], rl = ep[(16 + 2 * jj) * 256];
-                  float ih = ep[(2 * jj + 1) * 256], il = ep[(16 + 2 * jj + 1) * 256];
+                  const bool neg = kPairs * half + jj >= nb;
+                  float rh = ep[(2 * jj) * kDT], rl = ep[(8 * kCH + 2 * jj) * kDT];
+                  float ih = ep[(2 * jj + 1) * kDT], il = ep[(8 * kCH + 2 * jj + 1) * kDT];
                   if (neg && (mpr & 1)) { rh = -rh; rl = -rl; ih = -ih; il = -il; }
                   ff_add(cur[u].x, cur[u].y, rh, rl);
                   ff_add(cur[u].z, cur[u].w, ih, il);
@@ -680,10 +734,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       }
     }
     if (ctl && *abort_flag) {
-      // let the MMAs already issued finish before the TMEM is released, and
-      // the TMA loads already issued land before the CTA's shared memory goes
+      // let the MMAs already issued finish before the TMEM is released
       umma::commit(fin);
       wait_bar_all(fin, 0);
+    }
+    if (tma_thr && *abort_flag) {
+      // and the TMA loads already issued land before the CTA's shared memory goes
       for (int t = 0; t < kTS; ++t) {
         const int nt = n_tma > t ? (n_tma - t - 1) / kTS + 1 : 0;  // loads issued to stage t
         if (nt > 0) wait_bar_all(&tma_full[t], (uint32_t)(nt - 1) & 1u);
