@@ -44,10 +44,10 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 # absent here reports null.
 TRAFFIC = {
     (2048, 16, "mixed", 512, 1): {
-        "contract": [0.509e9, 3.029e9, 7.482e9, 13.976e9, 0.452e9, 2.409e9, 6.017e9, 11.443e9],
+        "contract": [0.506e9, 2.991e9, 7.453e9, 13.824e9, 0.437e9, 2.414e9, 6.369e9, 11.886e9],
         "delta": [0.125e9, 1.218e9, 3.383e9, 6.621e9, 0.125e9, 1.218e9, 3.383e9, 6.622e9],
         "theta": [3.193e9, 2.101e9],
-        "phi": [3.156e9, 3.205e9],
+        "phi": [3.156e9, 3.198e9],
     },
 }
 
