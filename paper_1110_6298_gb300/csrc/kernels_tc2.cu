@@ -30,7 +30,8 @@
 //                  (cp.async.bulk.tensor, this GPU's memory only, no
 //                  multicast) four K tiles ahead, and issues the MMAs of the
 //                  next K tile before its warp drains the current one.
-// Operands and their accumulators run in kS = 2 stages; stages are handed over with
+// Operands and their accumulators run in kS stages (4 with one spin group per
+// pass, 2 with two); stages are handed over with
 // mbarriers: TMA bytes -> producers -> MMA -> (producers, drain) -> MMA.  A
 // waiting thread is suspended in mbarrier.try_wait rather than spinning.
 // Every wait is bounded (2 s of wall clock): a wait that gives up records the
@@ -63,9 +64,11 @@ template <int NG>
 struct Layout {
   static constexpr int kTS = NG == 2 ? 3 : 4;                        // TMA stages (plane tiles in flight)
   // operand + accumulator stages (A in TMEM, B in smem, the accumulators they
-  // feed); 3 or 4 fit the TMEM with one spin group per pass but measured no
-  // faster at L = 2048 (31.0 ms per round trip with 2, 3 or 4 stages)
-  static constexpr int kS = 2;
+  // feed): with one spin group per pass, 4 fill the 512 TMEM columns (448 used)
+  // and let the producers, the MMA lane and the drain run up to 4 K tiles apart
+  // (27.1 ms per round trip at L = 2048, B = 16, against 28.8 with 2 stages and
+  // 28.3 with 3); two groups per pass have room for 2
+  static constexpr int kS = NG == 2 ? 2 : 4;
   static constexpr int kTmaStage = (1 + NG) * kTmaTile;             // row am + one spin row per group
   static constexpr int kBStage = NG * 3 * kBTile;
   static constexpr int kTmaOff = 0;                                  // 1024-aligned
@@ -78,19 +81,19 @@ struct Layout {
   // TMEM columns: accumulators (hi, corr) per stage and group, then A per
   // stage, group, K step and split (8 columns = 16 bf16 of K each)
   // hi.hi accumulator per stage and group; correction accumulator per item
-  // parity and group (it collects the five correction products of every K
-  // tile of an item and is read once, at the item's last K tile)
-  static constexpr int kAccCols = (kS + 2) * NG * 32;
+  // (kS of them in rotation) and group: it collects the five correction
+  // products of every K tile of an item and is read once, at the item's last
+  // K tile
+  static constexpr int kAccCols = 2 * kS * NG * 32;
   static constexpr int kCols = kAccCols + kS * NG * 2 * 3 * 8;
   static constexpr uint32_t kAlloc = kCols <= 256 ? 256u : 512u;
   static_assert(kCols <= 512, "TMEM budget");
   static_assert(kSmem <= 227 * 1024, "shared memory budget");
   __device__ static uint32_t acc_hi(int a, int g) { return (uint32_t)((a * NG + g) * 32); }
-  __device__ static uint32_t acc_corr(int ip, int g) { return (uint32_t)((kS * NG + ip * NG + g) * 32); }
-  // the correction accumulator of item k is reused by item k + 2, whose first
-  // MMAs wait (accempty) for the drain of a position at least kS later than
-  // item k's last one, which reads it: needs kS <= 2
-  static_assert(kS <= 2, "item-parity correction accumulators");
+  // the correction accumulator of item k is reused by item k + kS, whose
+  // first MMAs wait (accempty) for the drain of a position at least kS
+  // positions after item k's last one (every item has a K tile), which reads it
+  __device__ static uint32_t acc_corr(int ic, int g) { return (uint32_t)((kS * NG + ic * NG + g) * 32); }
   __device__ static uint32_t a_col(int s, int g, int ks, int sp) {
     return (uint32_t)(kAccCols + ((s * NG + g) * 2 + ks) * 24 + sp * 8);
   }
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     } P;  // TMA cursor (kTS positions ahead of the MMA cursor)
     struct MmaPos {
       int it, kt, nk, ngl, ip;
-    } Qm{};  // MMA cursor (ip: parity of the item among this CTA's items)
+    } Qm{};  // MMA cursor (ip: the item's correction accumulator, items in rotation)
     int n_tma = 0;  // TMA loads issued (stage t took those with index % kTS == t)
     int qm = 0;  // MMA position
     bool cok = true;
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       if (++P.kt >= P.nk) load_pos(P.it + G);
     };
     auto load_mpos = [&](int itp) {
-      Qm.ip = itp == (int)blockIdx.x ? 0 : Qm.ip ^ 1;
+      Qm.ip = itp == (int)blockIdx.x ? 0 : (Qm.ip + 1 == kS ? 0 : Qm.ip + 1);
       Qm.it = itp;
       Qm.kt = 0;
       if (itp >= A.nitems) return;
@@ -600,9 +603,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     for (int g = 0; g < NG; ++g)
 #pragma unroll
       for (int j = 0; j < 8 * kCH; ++j) hi[g][j] = lo[g][j] = 0.f;
-    int q = 0, ipd = 0;  // ipd: parity of the drained item
+    int q = 0, ipd = 0;  // ipd: correction accumulator of the drained item
     bool ok = drainer;
-    for (int it = blockIdx.x; ok && it < A.nitems; it += G, ipd ^= 1) {
+    for (int it = blockIdx.x; ok && it < A.nitems; it += G, ipd = (ipd + 1 == kS ? 0 : ipd + 1)) {
       const Item x = item_of<DIR>(A, it);
       const int ngl = min(NG, A.ng - x.gs * NG);
       for (int kt = 0; kt < x.nk; ++kt, ++q) {
