@@ -248,11 +248,11 @@ def delta_roofline(recursion, L, seconds, pk, fp32_issue, n_sm, mhz):
     issue_src = f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock in the timed region)"
     if recursion == "tn":
         units = sweeps * tn_units(L)
-        instr = 29 * units          # float-float: two products (7 each) and one multiply-add (15)
+        instr = 25 * units          # float-float: 2/b times the integer m (3), a product (7), a multiply-add (15)
         nbytes = 4 * units          # every quarter-plane element staged once in FP32
         t_i, t_b = instr / fp32_issue, nbytes / (pk["hbm_gbs"] * 1e9)
         issue = {"achieved": instr / seconds / 1e12, "peak": fp32_issue / 1e12, "unit": "T instr/s",
-                 "frac": t_i / seconds, "work": "29 FP32 instructions per quarter-plane element",
+                 "frac": t_i / seconds, "work": "25 FP32 instructions per quarter-plane element",
                  "peak_src": issue_src}
         hbm = {"achieved": nbytes / seconds / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": t_b / seconds,
                "work": "4 bytes (FP32 staging) per quarter-plane element", "peak_src": pk["src"]}

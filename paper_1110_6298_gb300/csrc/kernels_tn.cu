@@ -19,8 +19,9 @@
 // plane: one thread per column, one block per (plane, 128 or 256 columns), no waits
 // between blocks.  A block first forms the plane's recursion coefficients
 // 2/b(m') and a(m')/b(m') in shared memory (b = sqrt((l+m')(l-m'+1)),
-// a = sqrt((l-m')(l+m'+1))); each step then costs one float-float product by
-// the column index, one product and one multiply-add.  Every step writes one
+// a = sqrt((l-m')(l+m'+1))); each step then costs an exact scaling of 2/b by
+// the column index (3 FP32 instructions), one float-float product (7) and one
+// multiply-add (15).  Every step writes one
 // row of the FP32 staging plane, consecutive columns in consecutive threads,
 // so the stores are coalesced and the full quarter is written without a
 // transpose.
@@ -84,9 +85,14 @@ __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
   Scale2 sc;
   sc.set(E);
   st[(size_t)l * LD] = sc.apply(cur.x);
-  const float2 mf = make_float2((float)m, 0.f);
+  const float mf = (float)m;  // exact (m <= 2047)
   for (int mp = l; mp >= 1; --mp) {
-    const float2 t = NumFF::mul(c1[mp], mf);    // 2 m / b
+    // 2 m / b: the float-float 2 / b times the exact integer m -- TwoProduct of
+    // the high part, the low part's product added to its error, left
+    // unnormalised (the pair only feeds the fused multiply-add below)
+    const float2 c = c1[mp];
+    const float tp = __fmul_rn(c.x, mf);
+    const float2 t = make_float2(tp, __fmaf_rn(c.y, mf, __fmaf_rn(c.x, mf, -tp)));
     const float2 u = NumFF::mul(c2[mp], prev);  // (a / b) Delta_{m'+1}
     const float2 nw = NumFF::fma(t, cur, make_float2(-u.x, -u.y));
     prev = cur;
