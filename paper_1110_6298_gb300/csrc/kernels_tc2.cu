@@ -201,17 +201,21 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
   l = __fsub_rn(t, __fsub_rn(h, s));
 }
 
-// x (two values) -> bf16 pairs hi, mid, lo with x ~= hi + mid + lo
+// x (two values) -> bf16 pairs hi, mid, lo with x = hi + mid + lo exactly.
+// Each part is rounded to the nearest bf16 on the integer pipe -- half a bf16
+// ulp added to the bit pattern, the low 16 bits cleared -- so that hi and mid
+// are within half an ulp (ties away from zero), the remainders are exact and
+// lo, at most 8 significant bits, is exact as a bf16; the pairs are packed
+// (first value in the low half) by byte permutes.
+__device__ __forceinline__ uint32_t bf16_bits_rn(float x) { return (__float_as_uint(x) + 0x8000u) & 0xffff0000u; }
 __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& h, uint32_t& m, uint32_t& l) {
-  const __nv_bfloat162 hp = __floats2bfloat162_rn(x0, x1);
-  const float2 hf = __bfloat1622float2(hp);
-  const float r0 = x0 - hf.x, r1 = x1 - hf.y;
-  const __nv_bfloat162 mp = __floats2bfloat162_rn(r0, r1);
-  const float2 mf = __bfloat1622float2(mp);
-  const __nv_bfloat162 lp = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-  h = *reinterpret_cast<const uint32_t*>(&hp);
-  m = *reinterpret_cast<const uint32_t*>(&mp);
-  l = *reinterpret_cast<const uint32_t*>(&lp);
+  const uint32_t h0 = bf16_bits_rn(x0), h1 = bf16_bits_rn(x1);
+  const float r0 = __fsub_rn(x0, __uint_as_float(h0)), r1 = __fsub_rn(x1, __uint_as_float(h1));
+  const uint32_t m0 = bf16_bits_rn(r0), m1 = bf16_bits_rn(r1);
+  const float l0 = __fsub_rn(r0, __uint_as_float(m0)), l1 = __fsub_rn(r1, __uint_as_float(m1));
+  h = __byte_perm(h0, h1, 0x7632);
+  m = __byte_perm(m0, m1, 0x7632);
+  l = __byte_perm(__float_as_uint(l0), __float_as_uint(l1), 0x7632);
 }
 // split parts p of the six products, largest first: (A part, B part)
 __device__ __forceinline__ int split_a(int p) { return (0x210100 >> (4 * p)) & 0xF; }  // 0,0,1,0,1,2
@@ -291,10 +295,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     const int ks = warp >> 2, qd = warp & 3;
     const int r = 32 * qd + lane;                       // tile row = TMEM lane
     const uint32_t lane_addr = (uint32_t)(32 * qd) << 16;
-    const int pt = warp * 32 + lane;                    // B unit: group pt / 128, row n, 8-wide K chunk
-    const int bg = pt >> 7, bn = (pt >> 2) & 31, bkc = pt & 3;
-    // B cursor, two positions ahead of the A position: 8 consecutive K of row
-    // bn of group bg; the item's row pointer and signs are decoded once per item
+    // B unit of this thread: group bg, row n, kBV consecutive K of the 32-wide
+    // tile (NG = 2: 8 K, 128 threads per group; NG = 1: 4 K, all 256 threads)
+    constexpr int kBV = NG == 1 ? 4 : 8;
+    const int pt = warp * 32 + lane;
+    const int bg = NG == 1 ? 0 : pt >> 7;
+    const int bn = NG == 1 ? (pt >> 3) & 31 : (pt >> 2) & 31;
+    const int bk0 = NG == 1 ? 4 * (pt & 7) : 8 * (pt & 3);
+    // B cursor, two positions ahead of the A position: kBV consecutive K of
+    // row bn of group bg; the item's row pointer and signs are decoded once per item
     struct BPos {
       int it, kt, nk, k0;
       const float2* row;
@@ -308,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       if (it >= A.nitems) return;
       const Item x = item_of<DIR>(A, it);
       P.nk = x.nk;
-      P.k0 = x.kstart + 8 * bkc;  // m' (forward) or l (inverse)
+      P.k0 = x.kstart + bk0;  // m' (forward) or l (inverse)
       const int gidx = x.gs * NG + bg;
       if (bg >= NG || gidx >= A.ng) return;
       const SpinGroup& g = A.groups[gidx];
@@ -325,19 +334,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     // the end), and the (-1)^k of the -am fold is recorded as a sign mask, so
     // no instruction waits for the data until the buffer is stored two
     // positions later.
-    auto load_b = [&](float (&v)[8], uint32_t& sgn) {
+    auto load_b = [&](float (&v)[kBV], uint32_t& sgn) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      for (int i = 0; i < kBV; ++i) v[i] = 0.f;
       sgn = 0u;
       if (P.it >= A.nitems) return;
       if (P.valid) {
         const int k0 = P.k0 + kKT * P.kt;
         const float* src = reinterpret_cast<const float*>(P.row + k0) + (bn & 1);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < kBV; ++i)
           if (k0 + i < kend) v[i] = __ldg(src + 2 * i);
         // (-1)^m' (forward) or (-1)^l (inverse) of the -am fold: odd k negated
-        if (P.neg) sgn = (k0 & 1) ? 0x55u : 0xAAu;  // bit i set: entry k0 + i is odd
+        if (P.neg) sgn = ((k0 & 1) ? 0x55u : 0xAAu) & ((1u << kBV) - 1u);  // bit i set: entry k0 + i is odd
       }
       if (++P.kt >= P.nk) load_bpos(P.it + G);
     };
@@ -353,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       for (int g = 0; g < NG; ++g) spin[g] = g < ngl ? A.groups[x.gs * NG + g].s : 0;
     };
     load_item();
-    float b0[8], b1[8];
+    float b0[kBV], b1[kBV];
     uint32_t sg0, sg1;
     load_bpos(blockIdx.x);
     load_b(b0, sg0);
@@ -361,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     // One position: B of this position (loaded two positions ago) into
     // operand stage s, the B loads of the position two ahead, then A from the
     // plane tiles of TMA stage q % kTS into tensor memory.
-    auto body = [&](float (&cur)[8], uint32_t& csg) -> bool {
+    auto body = [&](float (&cur)[kBV], uint32_t& csg) -> bool {
       if (it >= A.nitems) return false;
       const int s = q % kS, ts = q % kTS;
       const uint32_t ph = (uint32_t)(q / kS) & 1u, tph = (uint32_t)(q / kTS) & 1u;
@@ -374,16 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       }
       umma::fence_after();
       if (bg < NG) {
-        uint32_t h[4], m[4], l[4];
+        uint32_t h[kBV / 2], m[kBV / 2], l[kBV / 2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) cur[i] = __uint_as_float(__float_as_uint(cur[i]) ^ (((csg >> i) & 1u) << 31));
+        for (int i = 0; i < kBV; ++i) cur[i] = __uint_as_float(__float_as_uint(cur[i]) ^ (((csg >> i) & 1u) << 31));
 #pragma unroll
-        for (int i = 0; i < 4; ++i) split_pair(cur[2 * i], cur[2 * i + 1], h[i], m[i], l[i]);
+        for (int i = 0; i < kBV / 2; ++i) split_pair(cur[2 * i], cur[2 * i + 1], h[i], m[i], l[i]);
         unsigned char* sb = smem + Ly::kBOff + s * Ly::kBStage + bg * 3 * kBTile;
-        const int off = umma::tile_off(bn, 8 * bkc, kKT / 8);
-        *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(sb + kBTile + off) = make_uint4(m[0], m[1], m[2], m[3]);
-        *reinterpret_cast<uint4*>(sb + 2 * kBTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        const int off = umma::tile_off(bn, bk0, kKT / 8);
+        if constexpr (kBV == 8) {
+          *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(sb + kBTile + off) = make_uint4(m[0], m[1], m[2], m[3]);
+          *reinterpret_cast<uint4*>(sb + 2 * kBTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        } else {
+          *reinterpret_cast<uint2*>(sb + off) = make_uint2(h[0], h[1]);
+          *reinterpret_cast<uint2*>(sb + kBTile + off) = make_uint2(m[0], m[1]);
+          *reinterpret_cast<uint2*>(sb + 2 * kBTile + off) = make_uint2(l[0], l[1]);
+        }
       }
       load_b(cur, csg);
       const float* T = reinterpret_cast<const float*>(smem + Ly::kTmaOff + ts * Ly::kTmaStage);
