@@ -188,7 +188,8 @@ cudaError_t launch_real_pack(const mw_plan* p, const double2* flm, double2* g, c
 // (dir 0: Eq. flm_wig into flm; dir 1: Eq. Fmm into F+)
 cudaError_t make_tc2_tensor_maps(mw_plan* o);
 cudaError_t make_tc2_items(mw_plan* p, int chunk);
-cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st);
+// rows l in [l0, l1) (l1 < 0: every row)
+cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st, int l0 = 0, int l1 = -1);
 cudaError_t launch_tc2(const mw_plan* p, const mw_plan* o, int dir, int l0, int l1c, double2* flm, cudaStream_t st);
 // Trapani-Navaza planes l in [lb, le) into staging slots l - l0 (mixed paths)
 cudaError_t launch_tn(const mw_plan* p, int l0, int lb, int le, cudaStream_t st);
@@ -211,13 +212,18 @@ struct WignerJob {
   int mode;
   const double2* flm_in;
   double2* flm_out;
+  // mode 1 on the BF16x3 path: flm_in's rows arrive chunk by chunk and the
+  // hook's `before` transposes each chunk's rows (no transposition up front)
+  bool chunked_flm = false;
 };
-// hook: if given, called after the contraction launches of every chunk of
-// planes [l0, l1) have been enqueued on st (the forward's f_lm rows l0..l1-1
-// are then final once st reaches that point).
+// hook: if given, fn is called after the contraction launches of every chunk
+// of planes [l0, l1) have been enqueued on st (the forward's f_lm rows
+// l0..l1-1 are then final once st reaches that point), and before (if not
+// null) just before them (after the chunk's recursion launch).
 struct ChunkHook {
   cudaError_t (*fn)(void* ctx, int l0, int l1);
   void* ctx;
+  cudaError_t (*before)(void* ctx, int l0, int l1) = nullptr;
 };
 cudaError_t run_wigner(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st, int* launches,
                        const ChunkHook* hook = nullptr);

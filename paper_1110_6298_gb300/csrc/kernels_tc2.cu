@@ -880,14 +880,15 @@ cudaError_t make_tc2_items(mw_plan* p, int chunk) {
 }
 
 // N_l f_lm in FP32, transposed to [B][M][L] (row m + L - 1, l contiguous; zero
-// for l < |m|): the inverse contraction reads 32 consecutive l of a row.
+// for l < |m|): the inverse contraction reads 32 consecutive l of a row.  Rows
+// l in [l0, l1) only (a chunk of planes whose f_lm rows have arrived).
 __global__ void k_flm_transpose(const double2* __restrict__ flm, const long long* __restrict__ foff,
-                                float2* __restrict__ out, int L) {
+                                float2* __restrict__ out, int L, int l0, int l1) {
   const int mi = blockIdx.x, b = blockIdx.y;
   const int M = 2 * L - 1, m = mi - (L - 1), am = m < 0 ? -m : m;
   const double2* src = flm + foff[b];
   float2* dst = out + ((size_t)b * M + mi) * L;
-  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+  for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     if (l >= am) {
       const double2 f = src[(size_t)l * l + l + m];
@@ -898,8 +899,10 @@ __global__ void k_flm_transpose(const double2* __restrict__ flm, const long long
   }
 }
 
-cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st) {
-  k_flm_transpose<<<dim3(p->M, p->B), 256, 0, st>>>(flm, p->d_foff, p->d_flmT, p->L);
+cudaError_t launch_flm_transpose(const mw_plan* p, const double2* flm, cudaStream_t st, int l0, int l1) {
+  if (l1 < 0 || l1 > p->L) l1 = p->L;
+  if (l0 >= l1) return cudaSuccess;
+  k_flm_transpose<<<dim3(p->M, p->B), 256, 0, st>>>(flm, p->d_foff, p->d_flmT, p->L, l0, l1);
   return cudaGetLastError();
 }
 

@@ -526,7 +526,7 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     mw_plan* q = jobs[c].q;
     e = cudaMemsetAsync(q->d_Gp, 0, sizeof(double2) * (size_t)q->B * q->M * q->L, st);
     if (e != cudaSuccess) return e;
-    if (!fp64) {
+    if (!fp64 && !jobs[c].chunked_flm) {
       e = (q->prec == MW_PREC_MIXED_BF16X3) ? launch_flm_transpose(q, jobs[c].flm_in, st)
                                             : launch_flm_to_f32(q, jobs[c].flm_in, st);
       if (e != cudaSuccess) return e;
@@ -549,6 +549,10 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     if (e != cudaSuccess) return e;
     span_d.end(nd);
     nl += nd;
+    if (hook && hook->before) {
+      e = hook->before(hook->ctx, l0, l1);
+      if (e != cudaSuccess) return e;
+    }
     StageSpan span_c(o, MW_STAGE_CONTRACT, st);
     int ncl = 0;
     for (int c = 0; c < nj; ++c) {
@@ -568,7 +572,7 @@ cudaError_t run_sweep(mw_plan* o, const WignerJob* jobs, int nj, cudaStream_t st
     }
     span_c.end(ncl);
     nl += ncl;
-    if (hook) {
+    if (hook && hook->fn) {
       e = hook->fn(hook->ctx, l0, l1);
       if (e != cudaSuccess) return e;
     }

@@ -529,10 +529,11 @@ cudaError_t theta_inverse_all(const mw_plan* c, cudaStream_t st) { return launch
 //            group start as soon as its copy has landed, while the next
 //            group's copy runs; the f_lm rows of a chunk of planes are
 //            copied back as soon as that chunk's contraction has written them.
-//   inverse: f_lm is copied in whole (the contraction reads every l of every
-//            map from the start); the theta and phi stages run group by
-//            group and each group's maps are copied back while the next
-//            group computes.
+//   inverse: f_lm is copied chunk of planes by chunk of planes (the rows
+//            l0..l1-1 a chunk's contraction reads), all copies queued at the
+//            start, each chunk's contraction waiting for its own; the theta
+//            and phi stages run group by group and each group's maps are
+//            copied back while the next group computes.
 // Device-side inputs or outputs skip their copies.  Returns after the host
 // output is written (st synchronised), as the staged path does.
 struct PinnedCopies {
@@ -573,6 +574,31 @@ cudaError_t copy_flm_rows(void* ctx, int l0, int l1) {
   const size_t off = (size_t)l0 * l0, width = sizeof(double2) * ((size_t)l1 * l1 - off);
   return cudaMemcpy2DAsync(c->flm_host + off, pitch, c->flm_dev + off, pitch, width, p->B, cudaMemcpyDeviceToHost,
                            c->cp);
+}
+
+// Inverse from a pinned host f_lm: every chunk's rows [l0^2, l1^2) of every map
+// are copied on the copy stream as soon as the call starts (one pitched copy
+// per chunk, each followed by an event); just before a chunk's contraction the
+// compute stream waits for that chunk's copy and, on the BF16x3 path,
+// transposes those rows, so only the first chunk's copy is exposed.
+struct PinnedUploads {
+  mw_plan* p;
+  cudaStream_t st;
+  std::vector<cudaEvent_t> ev;  // per chunk
+  int chunk;
+  const double2* flm_dev;
+  bool transpose;
+  int launches;
+};
+
+cudaError_t upload_ready(void* ctx, int l0, int l1) {
+  PinnedUploads* u = static_cast<PinnedUploads*>(ctx);
+  cudaError_t e = cudaStreamWaitEvent(u->st, u->ev[l0 / u->chunk], 0);
+  if (e == cudaSuccess && u->transpose) {
+    e = launch_flm_transpose(u->p, u->flm_dev, u->st, l0, l1);
+    ++u->launches;
+  }
+  return e;
 }
 
 cudaError_t run_pinned(mw_plan* p, bool forward, const void* in, void* out, bool in_dev, bool out_dev,
@@ -617,10 +643,30 @@ cudaError_t run_pinned(mw_plan* p, bool forward, const void* in, void* out, bool
     e = run_wigner(p, &job, 1, st, nl, out_dev ? nullptr : &hook);
     k = pc.next_ev;
   } else {
-    if (!in_dev) e = cudaMemcpyAsync((double2*)din, in, sizeof(double2) * (size_t)p->flm_elems,
-                                     cudaMemcpyHostToDevice, st);
-    WignerJob job{p, 1, din, nullptr};
-    if (e == cudaSuccess) e = run_wigner(p, &job, 1, st, nl);
+    if (!in_dev && p->prec != MW_PREC_MIXED_TF32X3) {
+      PinnedUploads up{p, st, {}, p->prec == MW_PREC_FP64 ? kChunk : p->chunk, din,
+                       p->prec == MW_PREC_MIXED_BF16X3, 0};
+      const size_t pitch = sizeof(double2) * (size_t)p->L * p->L;
+      for (int l0 = 0; l0 < p->L && e == cudaSuccess; l0 += up.chunk) {
+        const int l1 = l0 + up.chunk < p->L ? l0 + up.chunk : p->L;
+        const size_t off = (size_t)l0 * l0, width = sizeof(double2) * ((size_t)l1 * l1 - off);
+        e = cudaMemcpy2DAsync((double2*)din + off, pitch, (const double2*)in + off, pitch, width, (size_t)B,
+                              cudaMemcpyHostToDevice, cp);
+        cudaEvent_t ev = nullptr;
+        if (e == cudaSuccess) e = next_event(p, &k, &ev);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, cp);
+        up.ev.push_back(ev);
+      }
+      WignerJob job{p, 1, din, nullptr, up.transpose};
+      ChunkHook hook{nullptr, &up, upload_ready};
+      if (e == cudaSuccess) e = run_wigner(p, &job, 1, st, nl, &hook);
+      *nl += up.launches;
+    } else {
+      if (!in_dev) e = cudaMemcpyAsync((double2*)din, in, sizeof(double2) * (size_t)p->flm_elems,
+                                       cudaMemcpyHostToDevice, st);
+      WignerJob job{p, 1, din, nullptr};
+      if (e == cudaSuccess) e = run_wigner(p, &job, 1, st, nl);
+    }
     for (int b0 = 0; b0 < B && e == cudaSuccess; b0 += gm) {
       const int nb = b0 + gm <= B ? gm : B - b0;
       {
