@@ -44,18 +44,18 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 # absent here reports null.
 TRAFFIC = {
     (2048, 16, "mixed", 512, 1): {
-        "contract": [0.507e9, 3.021e9, 7.480e9, 14.111e9, 0.438e9, 2.435e9, 6.456e9, 12.425e9],
-        "delta": [0.125e9, 1.217e9, 3.383e9, 6.620e9, 0.125e9, 1.217e9, 3.382e9, 6.620e9],
-        "theta": [3.194e9, 2.100e9],
-        "phi": [3.156e9, 3.205e9],
+        "contract": [0.506e9, 3.025e9, 7.511e9, 14.190e9, 0.438e9, 2.423e9, 6.230e9, 12.444e9],
+        "delta": [0.125e9, 1.218e9, 3.382e9, 6.620e9, 0.125e9, 1.218e9, 3.383e9, 6.620e9],
+        "theta": [3.193e9, 2.101e9],
+        "phi": [3.156e9, 3.204e9],
     },
     (2048, 16, "mixed", 256, 1): {
-        "contract": [0.082e9, 0.461e9, 1.126e9, 2.124e9, 3.424e9, 4.955e9, 7.012e9, 8.972e9,
-                     0.068e9, 0.336e9, 0.792e9, 1.428e9, 2.234e9, 3.280e9, 4.494e9, 5.953e9],
-        "delta": [0.001e9, 0.102e9, 0.375e9, 0.782e9, 1.325e9, 2.000e9, 2.810e9, 3.754e9,
-                  0.001e9, 0.102e9, 0.375e9, 0.782e9, 1.324e9, 2.000e9, 2.810e9, 3.755e9],
-        "theta": [3.192e9, 2.100e9],
-        "phi": [3.157e9, 3.199e9],
+        "contract": [0.082e9, 0.461e9, 1.134e9, 2.127e9, 3.453e9, 4.991e9, 7.077e9, 9.117e9,
+                     0.068e9, 0.336e9, 0.800e9, 1.480e9, 2.378e9, 3.520e9, 4.911e9, 6.497e9],
+        "delta": [0.001e9, 0.103e9, 0.375e9, 0.782e9, 1.324e9, 2.000e9, 2.809e9, 3.754e9,
+                  0.001e9, 0.103e9, 0.374e9, 0.782e9, 1.325e9, 2.000e9, 2.809e9, 3.754e9],
+        "theta": [3.193e9, 2.101e9],
+        "phi": [3.156e9, 3.198e9],
     },
 }
 
