@@ -149,12 +149,19 @@ FftM<T> fft_m_of(const mw_plan* p) {
 // the length-M one: a ping-pong pair of M, or the Bluestein length NB in place
 int m_elems(const mw_plan* p) { return p->bluestein && p->fB.n > 2 * p->M ? p->fB.n : 2 * p->M; }
 // (vpt: values per thread of the Bluestein FFTs, kBsVPT in the forward and
-// inverse kernels, kFftVPT in the adjoints)
+// inverse kernels, kFftVPT in the adjoints).  In single precision the
+// mixed-radix route takes at most 256 threads: three 64 KB blocks per SM at
+// 2L-1 = 4095 then overlap one another's ring loads and FFT stages (the phi
+// stage measured 3.56 against 3.72 ms per round trip at L = 2048, B = 16 with
+// 512 threads, 3.94 with 384); double precision, one 128 KB block per SM,
+// keeps up to 512.
 int m_threads(const mw_plan* p, int vpt = kBsVPT) {
-  int b = 0;
-  if (p->bluestein) b = ((p->fB.n + vpt - 1) / vpt + 31) / 32 * 32;
   const int a = threads_pp(p->M);
-  return a > b ? a : b;
+  if (p->bluestein) {
+    const int b = ((p->fB.n + vpt - 1) / vpt + 31) / 32 * 32;
+    return a > b ? a : b;
+  }
+  return (p->prec != MW_PREC_FP64 && a > 256) ? 256 : a;
 }
 
 }  // namespace
