@@ -12,8 +12,9 @@
 // the start values, which fall to about exp(-0.28 l) at m = l / sqrt2 and to
 // 2^-l at m = l and leave the double range near l = 2560.  Here each column
 // carries its own power-of-two exponent: value = x 2^E with x a float-float
-// pair, rescaled by 2^-64 whenever |x| exceeds 2^64, and the start values come
-// from a host table of (float-float mantissa, exponent) pairs.
+// pair, rescaled by 2^-64 whenever |x| exceeds 2^64 (tested every second
+// step), and the start values come from a host table of (float-float
+// mantissa, exponent) pairs.
 //
 // Planes are independent given their top rows, and so are the columns of a
 // plane: one thread per column, one block per (plane, 128 or 256 columns), no waits
@@ -63,15 +64,14 @@ struct Scale2 {
 };
 
 __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
-  __shared__ float2 c1[kTMaxL + 1];  // 2 / b(m')
-  __shared__ float2 c2[kTMaxL + 1];  // a(m') / b(m')
+  __shared__ float4 cc[kTMaxL + 1];  // (2 / b(m'), a(m') / b(m')) as float-float pairs, one 16-byte load per step
   const int l = lb + (int)blockIdx.y;
   const int m0 = (int)(blockIdx.x * blockDim.x);
   if (m0 > l) return;  // whole block past the plane's last column (uniform)
   for (int mp = 1 + (int)threadIdx.x; mp <= l; mp += (int)blockDim.x) {
     const float2 ib = NumFF::mul(A.rsq[l + mp], A.rsq[l - mp + 1]);
-    c1[mp] = make_float2(2.0f * ib.x, 2.0f * ib.y);  // exact
-    c2[mp] = NumFF::mul(NumFF::mul(A.sq[l - mp], A.sq[l + mp + 1]), ib);
+    const float2 c2 = NumFF::mul(NumFF::mul(A.sq[l - mp], A.sq[l + mp + 1]), ib);
+    cc[mp] = make_float4(2.0f * ib.x, 2.0f * ib.y, c2.x, c2.y);  // 2 ib exact
   }
   __syncthreads();
   const int m = m0 + (int)threadIdx.x;
@@ -86,24 +86,41 @@ __global__ void __launch_bounds__(kTThreads) k_tn_planes(TnArgs A, int lb) {
   sc.set(E);
   st[(size_t)l * LD] = sc.apply(cur.x);
   const float mf = (float)m;  // exact (m <= 2047)
-  for (int mp = l; mp >= 1; --mp) {
-    // 2 m / b: the float-float 2 / b times the exact integer m -- TwoProduct of
-    // the high part, the low part's product added to its error, left
-    // unnormalised (the pair only feeds the fused multiply-add below)
-    const float2 c = c1[mp];
+  // one step m' -> m' - 1: 2 m / b is the float-float 2 / b times the exact
+  // integer m -- TwoProduct of the high part, the low part's product added to
+  // its error, left unnormalised (the pair only feeds the fused multiply-add)
+  auto step = [&](int mp) {
+    const float4 c = cc[mp];
     const float tp = __fmul_rn(c.x, mf);
     const float2 t = make_float2(tp, __fmaf_rn(c.y, mf, __fmaf_rn(c.x, mf, -tp)));
-    const float2 u = NumFF::mul(c2[mp], prev);  // (a / b) Delta_{m'+1}
+    const float2 u = NumFF::mul(make_float2(c.z, c.w), prev);  // (a / b) Delta_{m'+1}
     const float2 nw = NumFF::fma(t, cur, make_float2(-u.x, -u.y));
     prev = cur;
     cur = nw;
-    if (fabsf(cur.x) > 0x1p64f) {  // powers of two scale both parts exactly
+    st[(size_t)(mp - 1) * LD] = sc.apply(cur.x);
+  };
+  // One step multiplies max(|cur|, |prev|) by at most 2m/b + a/b <=
+  // sqrt(2l) + 1 < 2^7 (b >= sqrt(2l), a < b), so with both values below 2^64
+  // two steps stay below 2^78: the rescale test runs once per pair of steps,
+  // before the pair's stores take the scale.  Powers of two scale both parts
+  // exactly.
+  auto rescale = [&]() {
+    if (fmaxf(fabsf(cur.x), fabsf(prev.x)) > 0x1p64f) {
       cur = make_float2(cur.x * 0x1p-64f, cur.y * 0x1p-64f);
       prev = make_float2(prev.x * 0x1p-64f, prev.y * 0x1p-64f);
       E += 64;
       sc.set(E);
     }
-    st[(size_t)(mp - 1) * LD] = sc.apply(cur.x);
+  };
+  int mp = l;
+  for (; mp >= 2; mp -= 2) {
+    rescale();
+    step(mp);
+    step(mp - 1);
+  }
+  if (mp == 1) {
+    rescale();
+    step(1);
   }
 }
 
