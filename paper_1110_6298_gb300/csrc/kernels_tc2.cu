@@ -10,26 +10,35 @@
 // Delta_{m',-am} = (-1)^(l+m') Delta_{m',am} (Eq. wignerd_sym2 at pi/2).
 // Precision is that of kernels_tc.cu: A and B in FP32 split into three BF16
 // parts, six products per K = 16 step, the hi.hi product of every 32-wide K
-// tile in a fresh accumulator and the four correction products in a second
-// one, both summed across K tiles in float-float on the CUDA cores.
+// tile in a fresh accumulator (summed across K tiles in float-float on the
+// CUDA cores) and the five correction products in a second one that runs
+// over the whole work item.
 //
 // What is new is the data flow.  Each CTA (one per SM, 16 warps) walks a list
-// of work items (am, row tile, spin-group slice); a work item is a run of
-// 32-wide K tiles, and the K tiles of all the CTA's items form one pipelined
-// sequence:
-//   8 producer     form A for one row each (TMEM lane = row) for both spin
-//   warps          groups from one plane tile, split it, and store it straight
-//                  into tensor memory (tcgen05.st), so the MMAs read only B
-//                  from shared memory; they also split B into shared memory;
-//   8 drain warps  read the two accumulators per group (tcgen05.ld), add them
-//                  into float-float registers, release the accumulator, and
-//                  write the item's outputs after its last K tile;
-//   control        one lane of the first drain warp loads the FP32 plane tiles
-//                  of a K tile -- row am and the spin rows |s| of the 128
-//                  (forward) or 32 (inverse) planes -- with plain per-CTA TMA
-//                  (cp.async.bulk.tensor, this GPU's memory only, no
-//                  multicast) four K tiles ahead, and issues the MMAs of the
-//                  next K tile before its warp drains the current one.
+// of work items (am, row tile, spin-group slice of one or two groups); a work
+// item is a run of 32-wide K tiles, and the K tiles of all the CTA's items
+// form one pipelined sequence:
+//   8 producer     form A for one row each (TMEM lane = row) from the plane
+//   warps          tiles, split it, and store it straight into tensor memory
+//                  (tcgen05.st), so the MMAs read only B from shared memory;
+//                  they also split B into shared memory;
+//   MMA lane       issues the six split products of each K = 16 step
+//                  (tcgen05.mma, A from TMEM) and commits a stage's MMAs;
+//   TMA lane       loads the FP32 plane tiles of a K tile -- row am and the
+//                  spin row |s| of the 128 (forward) or 32 (inverse) planes --
+//                  with plain per-CTA TMA (cp.async.bulk.tensor, this GPU's
+//                  memory only, no multicast) up to four K tiles ahead;
+//   drain warps    read the accumulators (tcgen05.ld), add them into
+//                  float-float registers, release the accumulator, and write
+//                  the item's outputs after its last K tile.
+// With one group per pass the MMA and TMA lanes are lanes of their own (warps
+// 8 and 9) and warps 12..15 drain.  With two groups per pass lane 0 of warp 8
+// issues both, the MMAs of the next K tile before its warp drains the current
+// one with warps 9..15.  A two-group slice whose groups have the same spin (a
+// "twin": one batch of more than 8 maps of one spin) has one A for both: the
+// producers form it once and each product is one N = 64 MMA over both groups'
+// B rows, whose accumulator columns are adjacent; groups whose spins share
+// |s| load one spin row.
 // Operands and their accumulators run in kS stages (4 with one spin group per
 // pass, 2 with two); stages are handed over with
 // mbarriers: TMA bytes -> producers -> MMA -> (producers, drain) -> MMA.  A
@@ -53,8 +62,6 @@ namespace {
 constexpr int kKT = 32;                    // K per tile (two K = 16 MMA steps)
 constexpr int kRows = 128;                 // rows of a tile (TMEM lanes)
 constexpr int kN = 32;                     // accumulator columns per spin group
-constexpr int kWarps = 16;                 // 8 producer + 8 drain (one drain lane also controls)
-constexpr int kThreads = 32 * kWarps;
 constexpr int kTmaTile = 16384;            // one FP32 plane tile: 128 x 32 or 32 x 128 floats
 constexpr int kBTile = kN * kKT * 2;       // one BF16 split of B (2 KB)
 constexpr uint32_t kPolls = 1u << 24;
@@ -62,6 +69,10 @@ constexpr uint32_t kWaitNs = 2000000000u;  // 2 s: a healthy wait ends within mi
 
 template <int NG>
 struct Layout {
+  // warps: 8 producers, then (NG = 1) the MMA and TMA lanes' warps, two idle
+  // warps and 4 drain warps, or (NG = 2) 8 drain warps and one control warp
+  static constexpr int kWarps = NG == 2 ? 17 : 16;
+  static constexpr int kThreads = 32 * kWarps;
   static constexpr int kTS = NG == 2 ? 3 : 4;                        // TMA stages (plane tiles in flight)
   // operand + accumulator stages (A in TMEM, B in smem, the accumulators they
   // feed): with one spin group per pass, 4 fill the 512 TMEM columns (448 used)
@@ -70,6 +81,9 @@ struct Layout {
   // 28.3 with 3); two groups per pass have room for 2
   static constexpr int kS = NG == 2 ? 2 : 4;
   static constexpr int kTmaStage = (1 + NG) * kTmaTile;             // row am + one spin row per group
+  // B of a stage: split p of group g at (p * NG + g) * kBTile, so that the
+  // groups' tiles of one split are consecutive 32-row blocks of one 64-row
+  // operand (the twin pass below reads them with one N = 64 MMA)
   static constexpr int kBStage = NG * 3 * kBTile;
   static constexpr int kTmaOff = 0;                                  // 1024-aligned
   static constexpr int kBOff = kTS * kTmaStage;
@@ -236,7 +250,7 @@ __device__ __forceinline__ Item item_of(const Tc2Args& A, int it) {
 }
 
 template <int DIR, int NG>
-__global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUtensorMap tmap, Tc2Args A) {
+__global__ void __launch_bounds__(Layout<NG>::kThreads, 1) k_tc2(const __grid_constant__ CUtensorMap tmap, Tc2Args A) {
   using Ly = Layout<NG>;
   constexpr int kTS = Ly::kTS;
   extern __shared__ unsigned char smem_raw[];
@@ -253,13 +267,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + kTS + 3 * kS + 2);
   uint64_t* tma_empty = bar + kTS + 3 * kS + 3;  // [kTS] producers read a plane-tile stage (split roles)
   static_assert((2 * kTS + 3 * kS + 3) * 8 <= 256, "barrier area");
-  // Roles of warps 8..15.  One spin group per pass (NG = 1): lane 0 of warp 8
-  // issues the MMAs, lane 0 of warp 9 the TMA loads (refilling a stage once
-  // the producers report it read), and warps 12..15 drain all 32 accumulator
-  // columns of their lane quarter.  Two groups (NG = 2, whose float-float
-  // accumulators would not fit 4 drain warps' registers): lane 0 of warp 8
-  // does both issues between draining with the other 7 warps, each warp 16
-  // columns of its lane quarter.
+  // Roles of the warps after the producers.  One spin group per pass
+  // (NG = 1): lane 0 of warp 8 issues the MMAs, lane 0 of warp 9 the TMA
+  // loads (refilling a stage once the producers report it read), and warps
+  // 12..15 drain all 32 accumulator columns of their lane quarter.  Two groups
+  // (NG = 2, whose float-float accumulators would not fit 4 drain warps'
+  // registers): warps 8..15 drain, each 16 columns of each group in its lane
+  // quarter, and lane 0 of warp 16 issues the MMAs and refills a TMA stage
+  // once the MMAs of the position that read it have their operands.
   constexpr bool kSplit = NG == 1;
   constexpr int kCH = kSplit ? 4 : 2;        // 8-column accumulator chunks per drain thread
   constexpr int kDT = kSplit ? 128 : 256;    // drain threads
@@ -354,12 +369,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     int it = blockIdx.x, kt = 0, q = 0;
     Item x{};
     int ngl = 0, spin[NG];
+    bool twin = false, row1 = true;  // (NG = 2) groups of one spin; one spin row in the stage
     auto load_item = [&]() {
       if (it >= A.nitems) return;
       x = item_of<DIR>(A, it);
       ngl = min(NG, A.ng - x.gs * NG);
 #pragma unroll
       for (int g = 0; g < NG; ++g) spin[g] = g < ngl ? A.groups[x.gs * NG + g].s : 0;
+      if constexpr (NG == 2) {
+        twin = ngl == 2 && spin[0] == spin[1];
+        row1 = ngl < 2 || abs(spin[0]) == abs(spin[1]);
+      }
     };
     load_item();
     float b0[kBV], b1[kBV];
@@ -388,16 +408,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
         for (int i = 0; i < kBV; ++i) cur[i] = __uint_as_float(__float_as_uint(cur[i]) ^ (((csg >> i) & 1u) << 31));
 #pragma unroll
         for (int i = 0; i < kBV / 2; ++i) split_pair(cur[2 * i], cur[2 * i + 1], h[i], m[i], l[i]);
-        unsigned char* sb = smem + Ly::kBOff + s * Ly::kBStage + bg * 3 * kBTile;
+        unsigned char* sb = smem + Ly::kBOff + s * Ly::kBStage + bg * kBTile;
+        constexpr int kSp = NG * kBTile;  // split stride
         const int off = umma::tile_off(bn, bk0, kKT / 8);
         if constexpr (kBV == 8) {
           *reinterpret_cast<uint4*>(sb + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(sb + kBTile + off) = make_uint4(m[0], m[1], m[2], m[3]);
-          *reinterpret_cast<uint4*>(sb + 2 * kBTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          *reinterpret_cast<uint4*>(sb + kSp + off) = make_uint4(m[0], m[1], m[2], m[3]);
+          *reinterpret_cast<uint4*>(sb + 2 * kSp + off) = make_uint4(l[0], l[1], l[2], l[3]);
         } else {
           *reinterpret_cast<uint2*>(sb + off) = make_uint2(h[0], h[1]);
-          *reinterpret_cast<uint2*>(sb + kBTile + off) = make_uint2(m[0], m[1]);
-          *reinterpret_cast<uint2*>(sb + 2 * kBTile + off) = make_uint2(l[0], l[1]);
+          *reinterpret_cast<uint2*>(sb + kSp + off) = make_uint2(m[0], m[1]);
+          *reinterpret_cast<uint2*>(sb + 2 * kSp + off) = make_uint2(l[0], l[1]);
         }
       }
       load_b(cur, csg);
@@ -419,7 +440,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       }
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
-        const float* W = T + (1 + g) * (kTmaTile / 4);
+        if (g == 1 && twin) continue;  // the twin pass reads group 0's A for both groups
+        const float* W = T + (1 + (row1 ? 0 : g)) * (kTmaTile / 4);
         uint32_t hp[8], mp[8], lp[8];
         if (g < ngl) {
           const int sv = spin[g], as = sv < 0 ? -sv : sv;
@@ -489,24 +511,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     }
   } else {
     // ------------------------------------------------- control and drain
-    // NG = 2: lane 0 of warp 8 is the control thread: it loads the FP32 plane
-    // tiles by TMA kTS positions ahead and issues the MMAs of the next position
-    // before its warp drains the current one, so the tensor core works on
-    // position q+1 while the drain warps read position q.  NG = 1: the two
-    // issues run on their own lanes (warps 8 and 9) and never wait for a drain.
+    // The MMA lane and the TMA lane (one lane for both with NG = 2) never
+    // wait for a drain other than through the accempty barriers.
     const int qd = warp & 3;
     const int half = kSplit ? 0 : (warp - 8) >> 2;
     const int dt = tid - (kSplit ? 12 : 8) * 32;  // drain thread index
-    const bool drainer = kSplit ? warp >= 12 : true;
+    const bool drainer = kSplit ? warp >= 12 : warp < 16;
     const uint32_t lane_addr = (uint32_t)(32 * qd) << 16;
-    const bool ctl = warp == 8 && lane == 0;             // issues the MMAs (and, NG = 2, the TMA loads)
+    const bool ctl = lane == 0 && warp == (kSplit ? 8 : 16);  // issues the MMAs (and, NG = 2, the TMA loads)
     const bool tma_thr = kSplit ? (warp == 9 && lane == 0) : ctl;
     struct TmaPos {
-      int it, kt, nk, am, t0, kstart;
+      int it, kt, nk, am, t0, kstart, nsr;
       int asr[NG];
-    } P;  // TMA cursor (kTS positions ahead of the MMA cursor)
+    } P;  // TMA cursor (kTS positions ahead of the MMA cursor); nsr spin rows per stage
     struct MmaPos {
       int it, kt, nk, ngl, ip;
+      bool twin;
     } Qm{};  // MMA cursor (ip: the item's correction accumulator, items in rotation)
     int n_tma = 0;  // TMA loads issued (stage t took those with index % kTS == t)
     int qm = 0;  // MMA position
@@ -520,13 +540,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       const int ngl = min(NG, A.ng - y.gs * NG);
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
-        // a slice with fewer groups loads its last spin row again (bytes must match)
         const int sg = A.groups[y.gs * NG + min(g, ngl - 1)].s;
         P.asr[g] = sg < 0 ? -sg : sg;
       }
+      // groups whose spins share |s| (and a slice of one group) read one spin row
+      P.nsr = (NG == 2 && P.asr[0] == P.asr[NG - 1]) ? 1 : NG;
     };
     auto issue_tma = [&](int t) {
-      arrive_expect_tx(&tma_full[t], (uint32_t)((1 + NG) * kTmaTile));
+      arrive_expect_tx(&tma_full[t], (uint32_t)((1 + P.nsr) * kTmaTile));
       const uint32_t dst = tma_base + (uint32_t)(t * Ly::kTmaStage);
       int xx, zz;
       if (DIR == 0) { xx = kKT * P.kt; zz = P.t0 - A.l0; }               // 32 m' of 128 planes
@@ -534,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       tma_load_3d(dst, &tmap, xx, P.am, zz, &tma_full[t]);
 #pragma unroll
       for (int g = 0; g < NG; ++g)
-        tma_load_3d(dst + (uint32_t)((1 + g) * kTmaTile), &tmap, xx, P.asr[g], zz, &tma_full[t]);
+        if (g < P.nsr) tma_load_3d(dst + (uint32_t)((1 + g) * kTmaTile), &tmap, xx, P.asr[g], zz, &tma_full[t]);
       ++n_tma;
       if (++P.kt >= P.nk) load_pos(P.it + G);
     };
@@ -546,8 +567,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       const int4 v = A.items[itp];
       Qm.nk = v.w;
       Qm.ngl = min(NG, A.ng - v.z * NG);
+      Qm.twin = NG == 2 && Qm.ngl == 2 && A.groups[v.z * NG].s == A.groups[v.z * NG + NG - 1].s;
     };
     const uint32_t idesc = umma::idesc_bf16_f32(kRows, kN);
+    const uint32_t idesc2 = umma::idesc_bf16_f32(kRows, 2 * kN);  // both groups of a twin pass
     const uint64_t bdesc0 = umma::smem_desc(b_base, 128, (kKT / 8) * 128);
     // MMAs of the MMA cursor's position, then the TMA kTS positions ahead
     auto mma_step = [&]() {
@@ -568,7 +591,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       const uint32_t acc_s = tmem + Ly::acc_hi(st, 0), corr_s = tmem + Ly::acc_corr(Qm.ip, 0);
       const uint32_t a_s = tmem + Ly::a_col(st, 0, 0, 0);
       const bool first = Qm.kt == 0;  // the item's first K tile starts its correction accumulator
-      auto issue = [&](auto ngc) {
+      // NGC groups of N = 32 with their own A; a twin pass (two groups of one
+      // spin, so one A) as one N = 64 MMA per product over both groups' B
+      // rows and accumulator columns, which are adjacent
+      auto issue = [&](auto ngc, uint32_t id) {
         constexpr int NGC = decltype(ngc)::value;
 #pragma unroll
         for (int k2 = 0; k2 < 2; ++k2)
@@ -578,11 +604,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
             for (int g = 0; g < NGC; ++g)
               mma_ta((p == 0 ? acc_s : corr_s) + (uint32_t)(g * 32),
                      a_s + (uint32_t)((g * 2 + k2) * 24 + split_a(p) * 8),
-                     bd_s + (uint64_t)((((g * 3 + split_b(p)) * kBTile) + k2 * 256) >> 4), idesc,
+                     bd_s + (uint64_t)((((split_b(p) * NG + g) * kBTile) + k2 * 256) >> 4), id,
                      (p == 0) ? (k2 > 0) : !(first && k2 == 0 && p == 1));
       };
-      if (NG == 2 && Qm.ngl == 2) issue(std::integral_constant<int, NG>{});
-      else issue(std::integral_constant<int, 1>{});
+      if (NG == 2 && Qm.twin) issue(std::integral_constant<int, 1>{}, idesc2);
+      else if (NG == 2 && Qm.ngl == 2) issue(std::integral_constant<int, NG>{}, idesc);
+      else issue(std::integral_constant<int, 1>{}, idesc);
       umma::commit(&done[st]);
       // the plane tiles of this position were read (full was observed): refill
       if (!kSplit && P.it < A.nitems) issue_tma(qm % kTS);
@@ -595,11 +622,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
     }
     if (ctl) {
       load_mpos(blockIdx.x);
-      if (kSplit) {
-        while (cok && Qm.it < A.nitems) mma_step();
-      } else {
-        mma_step();  // position 0
-      }
+      while (cok && Qm.it < A.nitems) mma_step();
     } else if (kSplit && tma_thr) {
       // refill the stage of position qt with position qt + kTS once the
       // producers have read it
@@ -626,10 +649,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc2(const __grid_constant__ CUt
       for (int kt = 0; kt < x.nk; ++kt, ++q) {
         const int s = q % kS;
         const uint32_t ph = (uint32_t)(q / kS) & 1u;
-        if (!kSplit && warp == 8) {
-          if (ctl) mma_step();  // position q + 1
-          __syncwarp();
-        }
         if (!__all_sync(0xffffffffu, wait_bar(&done[s], ph, abort_flag))) {
           if (lane == 0) fail();
           ok = false;
@@ -807,7 +826,7 @@ cudaError_t launch_t(const mw_plan* p, const mw_plan* o, int l0, int l1c, const 
   a.bsrc = bsrc; a.nl = p->d_nl; a.flm = flm; a.foff = p->d_foff;
   a.Fp = p->d_Gp; a.err = p->d_err;
   const int grid = nitems < nsm ? nitems : nsm;
-  k_tc2<DIR, NG><<<grid, kThreads, Ly::kSmem, st>>>(DIR == 0 ? o->tmap_fwd : o->tmap_inv, a);
+  k_tc2<DIR, NG><<<grid, Ly::kThreads, Ly::kSmem, st>>>(DIR == 0 ? o->tmap_fwd : o->tmap_inv, a);
   return cudaGetLastError();
 }
 
