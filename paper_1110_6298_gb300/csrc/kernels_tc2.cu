@@ -279,6 +279,12 @@ __global__ void __launch_bounds__(Layout<NG>::kThreads, 1) k_tc2(const __grid_co
   constexpr int kCH = kSplit ? 4 : 2;        // 8-column accumulator chunks per drain thread
   constexpr int kDT = kSplit ? 128 : 256;    // drain threads
   constexpr int kPairs = 4 * kCH;            // (map, sign) columns per drain thread
+  // the epilogue's output loops: fully unrolled with one group per pass; with
+  // two, whose second group's sums are live during the first one's epilogue
+  // (at 96 registers a thread), partly rolled, which spills less (24.5
+  // against 25.3 ms per round trip at L = 2048, B = 16)
+  constexpr int kUnrollFwd = NG == 2 ? 2 : kPairs;
+  constexpr int kUnrollInv = NG == 2 ? 1 : kPairs / 4;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   if (tid == 0) {
@@ -715,7 +721,7 @@ __global__ void __launch_bounds__(Layout<NG>::kThreads, 1) k_tc2(const __grid_co
 #pragma unroll
               for (int jj = 0; jj < kPairs; ++jj) base[jj] = mapj[jj] >= 0 ? A.foff[mapj[jj]] : 0;
               const double nl = ((sv & 1) ? -1.0 : 1.0) * A.nl[l];
-#pragma unroll
+#pragma unroll kUnrollFwd
               for (int jj = 0; jj < kPairs; ++jj) {
                 if (mapj[jj] < 0) continue;
                 const bool neg = kPairs * half + jj >= nb;
@@ -740,7 +746,7 @@ __global__ void __launch_bounds__(Layout<NG>::kThreads, 1) k_tc2(const __grid_co
           } else {
             const int mpr = row;
             if (mpr < A.L && mpr < A.l1c) {
-#pragma unroll
+#pragma unroll kUnrollInv
               for (int j0 = 0; j0 < kPairs; j0 += 4) {  // four read-modify-writes in flight at a time
                 float4* dst[4];
                 float4 cur[4];
