@@ -40,22 +40,14 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 # stage kernels in one round trip (inverse launches first), keyed by (L, B,
 # precision, planes per launch, spin groups per contraction pass), from a
 # 1-pass ncu capture of the headline round trip (bench.py --headline-only
-# --tuning 512,1,128) with the kernels as they are now; a stage or tuning
-# absent here reports null.
+# --tuning CHUNK,GROUPS,128) with the kernels as they are now; a stage or
+# tuning absent here reports null.
 TRAFFIC = {
-    (2048, 16, "mixed", 512, 1): {
-        "contract": [0.506e9, 3.025e9, 7.511e9, 14.190e9, 0.438e9, 2.423e9, 6.230e9, 12.444e9],
-        "delta": [0.125e9, 1.218e9, 3.382e9, 6.620e9, 0.125e9, 1.218e9, 3.383e9, 6.620e9],
-        "theta": [3.193e9, 2.101e9],
-        "phi": [3.156e9, 3.204e9],
-    },
-    (2048, 16, "mixed", 256, 1): {
-        "contract": [0.082e9, 0.461e9, 1.134e9, 2.127e9, 3.453e9, 4.991e9, 7.077e9, 9.117e9,
-                     0.068e9, 0.336e9, 0.800e9, 1.480e9, 2.378e9, 3.520e9, 4.911e9, 6.497e9],
-        "delta": [0.001e9, 0.103e9, 0.375e9, 0.782e9, 1.324e9, 2.000e9, 2.809e9, 3.754e9,
-                  0.001e9, 0.103e9, 0.374e9, 0.782e9, 1.325e9, 2.000e9, 2.809e9, 3.754e9],
-        "theta": [3.193e9, 2.101e9],
-        "phi": [3.156e9, 3.198e9],
+    (2048, 16, "mixed", 512, 2): {
+        "contract": [0.512e9, 2.808e9, 7.779e9, 13.679e9, 0.435e9, 2.507e9, 6.270e9, 11.810e9],
+        "delta": [0.125e9, 1.220e9, 3.386e9, 6.624e9, 0.126e9, 1.220e9, 3.386e9, 6.624e9],
+        "theta": [3.199e9, 2.101e9],
+        "phi": [3.155e9, 3.247e9],
     },
 }
 
@@ -508,6 +500,40 @@ def run_ours(args, rank, world, local_rank):
                    "ms_per_step": rb_ms / K, "rel_err": rb_err, "stage_ms_per_step": rb_stages,
                    "what": "the same round trip with Risbo's recursion (MW_FLAG_DELTA_RISBO)"}
 
+    # ---- a batch of one spin: B spin-0 maps with the headline's tuning; with
+    # two spin groups per contraction pass the two groups of 8 maps share one
+    # A operand (one N = 64 MMA per split product)
+    os_line = None
+    if args.precision != "fp64" and not args.no_configs:
+        g1 = wl.rng(41)
+        f1 = torch.from_numpy(np.stack([wl.gaussian_flm(g1, L, 0, wl.cl_red) for _ in range(B)])).to(dev)
+        p1 = mw.Plan(L, [0] * B, precision=args.precision, graph=True)
+        p1.set_tuning(tuning["chunk"], tuning["groups"], tuning["tn_threads"])
+        o1 = torch.empty_like(f1)
+
+        def rt_1():
+            p1.inverse(f1, out=maps)
+            p1.forward(maps, out=o1)
+        for _ in range(W):
+            rt_1()
+        torch.cuda.synchronize(dev)
+        p1.sync()
+        os_ms, _ = timed(rt_1, K)
+        os_err = float((o1 - f1).abs().max().item() / f1.abs().max().item())
+
+        def call_1():
+            p1.inverse(f1, out=maps)
+            n = p1.last_launches
+            p1.forward(maps, out=o1)
+            return n + p1.last_launches
+        os_stages, _ = stage_breakdown(p1, call_1, 2, dev)
+        p1.close()
+        del p1, f1, o1
+        os_line = {"value": whole_job_value(world, B, K, os_ms / 1e3), "unit": "transforms/s",
+                   "ms_per_step": os_ms / K, "rel_err": os_err, "stage_ms_per_step": os_stages,
+                   "what": f"the same round trip on {B} spin-0 maps (one spin: the two spin groups of a "
+                           "contraction pass share one A operand), the headline's tuning"}
+
     # ---- a prime 2L-1: L = 2047 (4093) runs its ring and theta DFTs by
     # Bluestein's convolution; its phi + theta time against L = 2048's
     pr_line = None
@@ -663,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
                  "ms_per_step": r_ms / K, "rel_err": r_err,
                  "what": f"round trip of {B} real spin-0 maps (Sec. IV-G), uniform[-1,1] coefficients"},
         "risbo": rb_line,
+        "one_spin": os_line,
         "prime_l2047": pr_line,
         "fused": {"value": whole_job_value(world, B, K, fu_ms / 1e3), "unit": "transforms/s",
                   "ms_per_step": fu_ms / K, "rel_err": fu_err,
