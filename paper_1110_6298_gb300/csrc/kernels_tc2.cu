@@ -14,10 +14,10 @@
 // CUDA cores) and the five correction products in a second one that runs
 // over the whole work item.
 //
-// What is new is the data flow.  Each CTA (one per SM, 16 warps) walks a list
-// of work items (am, row tile, spin-group slice of one or two groups); a work
-// item is a run of 32-wide K tiles, and the K tiles of all the CTA's items
-// form one pipelined sequence:
+// What is new is the data flow.  Each CTA (one per SM; 16 warps, 17 with two
+// groups per pass) walks a list of work items (am, row tile, spin-group slice
+// of one or two groups); a work item is a run of 32-wide K tiles, and the K
+// tiles of all the CTA's items form one pipelined sequence:
 //   8 producer     form A for one row each (TMEM lane = row) from the plane
 //   warps          tiles, split it, and store it straight into tensor memory
 //                  (tcgen05.st), so the MMAs read only B from shared memory;
