@@ -279,7 +279,7 @@ def delta_roofline(recursion, L, seconds, pk, fp32_issue, n_sm, mhz):
     return out
 
 
-def survey_delta_stage(L, t_d, fp64_tflops, tc_flops, tc_peak, c_bytes, hbm_gbs):
+def fp64_rate_delta_stage(L, t_d, fp64_tflops, tc_flops, tc_peak, c_bytes, hbm_gbs):
     """The Delta stage (recursion + contractions, t_d seconds per round trip)
     against the formula that counts the recursion at the FP64 rate: max(7
     flops per element of two recursions / FP64 peak, products / tensor peak,
@@ -646,7 +646,7 @@ def run_ours(args, rank, world, local_rank):
                    "recursion": recursion,
                    "bounds_ms": {"recursion": 1e3 * bounds[0], "contraction_tensor": 1e3 * bounds[1],
                                  "contraction_hbm": 1e3 * bounds[2]},
-                   "fp64_rate_formula": survey_delta_stage(L, t_d, pk["fp64_tflops"], tc_flops, tc_peak, c_bytes,
+                   "fp64_rate_formula": fp64_rate_delta_stage(L, t_d, pk["fp64_tflops"], tc_flops, tc_peak, c_bytes,
                                                            pk_hbm)}
     if rb_line is not None:
         rb_line["delta_roofline"] = delta_roofline("risbo_ff", L, rb_line["stage_ms_per_step"]["delta"] / 1e3, pk,

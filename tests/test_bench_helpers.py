@@ -54,11 +54,11 @@ def test_delta_roofline_consistent(rec):
             assert "fp32_issue" in d
 
 
-def test_survey_formula_and_job_value():
+def test_fp64_rate_formula_and_job_value():
     L = 2048
     tc = 2 * bench.contraction_units(L, [0] * 8 + [2] * 8) * 4
     cb = bench.contraction_bytes(L, 16, "mixed")
-    r = bench.survey_delta_stage(L, 0.0564, PK["fp64_tflops"], tc, PK["bf16_tflops"], cb, PK["hbm_gbs"])
+    r = bench.fp64_rate_delta_stage(L, 0.0564, PK["fp64_tflops"], tc, PK["bf16_tflops"], cb, PK["hbm_gbs"])
     rec_oct = 2 * 7 * bench.risbo_units(L) / (PK["fp64_tflops"] * 1e12)
     assert abs(r["roofline_ms"] - 1e3 * rec_oct) < 1e-9
     assert r["frac_quarter_plane_units"] > r["frac"]
